@@ -1,0 +1,119 @@
+"""Degree-predictor MLP: FP64 reference forward, backward and Adam step.
+
+TEST INFRASTRUCTURE: checks the CUDA training and inference kernels.
+The network maps per-vector features to a filter degree (the learned
+replacement for the Single Optimization rule of Sec. 3.2; the paper has
+no such network).
+
+Architecture: x (F) -> tanh(W1 x + b1) (H) -> tanh(W2 h1 + b2) (H) ->
+y = W3 h2 + b3 (1).  Loss: 0.5 * mean((y - target)^2).  Adam follows
+Kingma and Ba, ICLR 2015, Algorithm 1.
+
+Features of one active column (``features``):
+  x0 = clip(t, -8, 8),  t = (lam - c)/e   (Ritz value in the filter frame)
+  x1 = log10(r) / 10                      (residual)
+  x2 = acosh(max(|t|, 1))                 (analytic decay per degree)
+  x3 = clip((gamma - c)/e, -8, 8)         (filter bounds: lower end)
+  x4 = step / 10                          (index in the sequence)
+The target is degree / 60; a prediction y gives degree
+clamp(round(60 y), 4, 60).
+
+Label (``degree_label``): with r_b the residual that chose degree m and
+r_a the residual after filtering with it, kappa = ln(r_b/r_a)/m is the
+realised decay per degree and m* = ceil(ln(r_b/tol)/kappa), clamped to
+[4, 60].  Parity unpinned for the label definition (not in the paper).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+N_FEAT = 5
+HIDDEN = 64
+DEG_LO, DEG_HI, DEG_SCALE = 4, 60, 60.0
+
+
+def init_params(seed: int, n_feat: int = N_FEAT, hidden: int = HIDDEN) -> dict:
+    """Glorot-uniform weights, zero biases."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+
+    def glorot(o, i):
+        lim = math.sqrt(6.0 / (i + o))
+        return rng.uniform(-lim, lim, size=(o, i))
+
+    return {"W1": glorot(hidden, n_feat), "b1": np.zeros(hidden),
+            "W2": glorot(hidden, hidden), "b2": np.zeros(hidden),
+            "W3": glorot(1, hidden), "b3": np.zeros(1)}
+
+
+def features(ritz, resid, c, e, gamma, step):
+    t = (np.asarray(ritz, dtype=np.float64) - c) / e
+    r = np.maximum(np.asarray(resid, dtype=np.float64), 1e-300)
+    x = np.empty((t.size, N_FEAT))
+    x[:, 0] = np.clip(t, -8.0, 8.0)
+    x[:, 1] = np.log10(r) / 10.0
+    x[:, 2] = np.arccosh(np.maximum(np.abs(t), 1.0))
+    x[:, 3] = np.clip((gamma - c) / e, -8.0, 8.0)
+    x[:, 4] = step / 10.0
+    return x
+
+
+def degree_label(r_before, r_after, m_used, tol):
+    rb = np.asarray(r_before, dtype=np.float64)
+    ra = np.maximum(np.asarray(r_after, dtype=np.float64), 1e-300)
+    m = np.asarray(m_used, dtype=np.float64)
+    kappa = np.log(rb / ra) / m
+    lab = np.full(rb.size, float(DEG_HI))
+    ok = kappa > 1e-6
+    with np.errstate(divide="ignore", invalid="ignore"):
+        lab[ok] = np.ceil(np.log(np.maximum(rb[ok], tol) / tol) / kappa[ok])
+    return np.clip(lab, DEG_LO, DEG_HI)
+
+
+def forward(p: dict, x):
+    z1 = x @ p["W1"].T + p["b1"]
+    h1 = np.tanh(z1)
+    z2 = h1 @ p["W2"].T + p["b2"]
+    h2 = np.tanh(z2)
+    y = h2 @ p["W3"].T + p["b3"]
+    return y[:, 0], {"x": x, "h1": h1, "h2": h2}
+
+
+def loss_and_grads(p: dict, x, target):
+    """0.5 * mean((y - target)^2) and its gradient (backpropagation)."""
+    y, cache = forward(p, x)
+    B = x.shape[0]
+    d = (y - target) / B
+    loss = 0.5 * float(np.mean((y - target) ** 2))
+    h1, h2 = cache["h1"], cache["h2"]
+    g = {"W3": d[None, :] @ h2, "b3": np.array([d.sum()])}
+    dh2 = d[:, None] * p["W3"]
+    dz2 = dh2 * (1.0 - h2 ** 2)
+    g["W2"] = dz2.T @ h1
+    g["b2"] = dz2.sum(axis=0)
+    dh1 = dz2 @ p["W2"]
+    dz1 = dh1 * (1.0 - h1 ** 2)
+    g["W1"] = dz1.T @ x
+    g["b1"] = dz1.sum(axis=0)
+    return loss, g
+
+
+def adam_step(p: dict, g: dict, state: dict, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma and Ba, Algorithm 1), in place on p."""
+    t = state.get("t", 0) + 1
+    state["t"] = t
+    for kname in p:
+        mo = state.setdefault("m_" + kname, np.zeros_like(p[kname]))
+        ve = state.setdefault("v_" + kname, np.zeros_like(p[kname]))
+        mo[...] = b1 * mo + (1 - b1) * g[kname]
+        ve[...] = b2 * ve + (1 - b2) * g[kname] ** 2
+        mh = mo / (1 - b1 ** t)
+        vh = ve / (1 - b2 ** t)
+        p[kname] = p[kname] - lr * mh / (np.sqrt(vh) + eps)
+    return p
+
+
+def predict_degrees(p: dict, x):
+    y, _ = forward(p, x)
+    return np.clip(np.rint(DEG_SCALE * y), DEG_LO, DEG_HI).astype(np.int64)
