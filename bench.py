@@ -1,0 +1,354 @@
+"""Benchmark: seconds per eigenproblem and Chebyshev-filter TFLOP/s of the
+GB300 ChFSI on a correlated sequence of dense complex Hermitian problems.
+
+Workload (default): 10 correlated complex128 problems, n = 4096, nev = 256,
+nex = 64, spectrum with 300 low eigenvalues in [-3, -1] and the bulk in
+[0, 20], H_{l+1} = U H_l U^H + 1e-4 diag(d), U = exp(1e-3 i A); problem 1
+starts from a random block, problem l+1 from problem l's Ritz vectors;
+tolerance 1e-10.  One step = solving the whole sequence.  Every H is
+268 MB (larger than the 129 MB L2), so no L2 flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank solves its own
+replica of the sequence (independent problems shard with no exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "filter TFLOP/s and s per eigenproblem at resid≤1e-10: mixed+learned vs FP64"
+UNIT = "s/eigenproblem"
+SEQ_SEED_OFFSET = 2000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="fp64")
+    ap.add_argument("--n", type=int, default=None, help="override n (smaller test runs)")
+    ap.add_argument("--length", type=int, default=None)
+    ap.add_argument("--fp64-compare", type=int, default=0,
+                    help="also time the plain FP64 path on this many problems")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace('.', '').isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace('.', '').isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def sizes(cfg, n):
+    if n == cfg.n:
+        return cfg.nev, cfg.nex
+    return max(1, cfg.nev * n // cfg.n), max(1, cfg.nex * n // cfg.n)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """The oracle (plain FP64 NumPy ChFSI) on the host cores: each step
+    solves problem 1 (random start) and problem 2 (warm start) of the same
+    sequence; the value extrapolates to the 10-problem sequence as
+    (t1 + 9 t2) / 10."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import torch
+    import oracle
+    from workloads.synthetic import CONFIGS, random_block
+    cfg = CONFIGS[2]
+    n = args.n or cfg.n
+    nev, nex = sizes(cfg, n)
+    length = args.length or cfg.length
+    dev = torch.device("cuda:0") if torch.cuda.is_available() else None
+    from workloads.synthetic import config_sequence
+    Hs, lam = config_sequence(cfg, 14044161 + 2000, length=2, n=n, device=dev)
+    Hs = [h.cpu().numpy() if dev is not None else h for h in Hs]
+    X0 = random_block(n, nev + nex, 14044161 + 2500)
+    times = []
+    for it in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r1 = oracle.chfsi(Hs[0], nev, nex, X0, cfg.tol)
+        t1 = time.perf_counter()
+        r2 = oracle.chfsi(Hs[1], nev, nex, r1["X"], cfg.tol,
+                          warm=(r1["evals"][0], r1["evals"][-1]))
+        t2 = time.perf_counter()
+        if it >= args.warmup:
+            times.append((t1 - t0, t2 - t1))
+    t1m = float(np.mean([a for a, _ in times]))
+    t2m = float(np.mean([b for _, b in times]))
+    val = (t1m + (length - 1) * t2m) / length
+    cores = os.cpu_count()
+    sample = (f"problems 1 (random start) and 2 (warm start) of the n={n} sequence per step; "
+              f"value = (t1 + {length - 1} t2)/{length}")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * (t1m + t2m),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"correlated sequence of {length} complex128 Hermitian problems, "
+                               f"n={n}, nev={nev}, nex={nex}, tol 1e-10",
+                   "l2": "inputs larger than L2"},
+        "cpu_baseline": {"kind": "oracle", "value": val, "unit": UNIT, "cores": cores,
+                         "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "loops": [int(r1["loops"]), int(r2["loops"])],
+    }))
+
+
+def cpu_baseline_sample(Hs_host, nev, nex, tol, X0, length):
+    """Oracle on the host cores, bounded: problem 1 (random start) and
+    problem 2 (warm start) of the sequence, extrapolated like the
+    reference arm."""
+    import oracle
+    t0 = time.perf_counter()
+    r1 = oracle.chfsi(Hs_host[0], nev, nex, X0, tol)
+    t1 = time.perf_counter()
+    oracle.chfsi(Hs_host[1], nev, nex, r1["X"], tol, warm=(r1["evals"][0], r1["evals"][-1]))
+    t2 = time.perf_counter()
+    val = ((t1 - t0) + (length - 1) * (t2 - t1)) / length
+    return {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"problems 1 (random start) and 2 (warm start), value = (t1 + "
+                      f"{length - 1} t2)/{length}; t1 {t1 - t0:.2f} s, t2 {t2 - t1:.2f} s"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1404_4161_gb300.build import build
+    if rank == 0:
+        build()
+    if ws > 1:
+        dist.barrier()
+    from paper_1404_4161_gb300 import _lib as L
+    from paper_1404_4161_gb300.solver import Chfsi, colmajor
+    from workloads.synthetic import CONFIGS, random_block
+
+    cfg = CONFIGS[2]
+    n = args.n or cfg.n
+    nev, nex = sizes(cfg, n)
+    k = nev + nex
+    length = args.length or cfg.length
+    from workloads.synthetic import config_sequence
+    Hs, lam = config_sequence(cfg, 14044161 + 2000, length=length, n=n, device=dev)
+    Hcs = [colmajor(h) for h in Hs]  # H Hermitian: column-major copy of H
+    del Hs
+    X0 = random_block(n, k, 14044161 + 2500)
+    X0c = colmajor(torch.from_numpy(X0).to(dev))
+    torch.cuda.synchronize()
+
+    prec = L.PREC_MIXED if args.precision == "mixed" else L.PREC_FP64
+    s = Chfsi(precision=prec)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        Xc = X0c.clone()
+        ev, sts, rc = s.solve_sequence(Hcs, nev, nex, Xc, cfg.tol)
+        return ev, sts, rc, Xc
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    stats_all = []
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        ev, sts, rc, Xc = step()
+        stats_all.append(sts)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    sec_per_problem = ms / 1e3 / (length * ws)  # all ranks' problems / max time
+
+    # correctness of the timed result (residual certificate, on the device)
+    Xl = Xc.t()[:, :nev]
+    Hl = Hcs[-1].t()
+    R = torch.linalg.vector_norm(Hl @ Xl - Xl * ev[-1, :nev].to(Xl.dtype), dim=0)
+    max_res = float(R.max()) / max(abs(float(lam[0])), abs(float(lam[-1])))
+
+    last = stats_all[-1]
+    filt_ms = sum(x["ms_filter"] for x in last)
+    filt_flops = sum(x["filter_flops"] for x in last)
+    filt_launch = sum(x["filter_launches"] for x in last)
+    launches = sum(sum(x["launches"] for x in sts) for sts in stats_all)
+    lowp_flops = sum(8.0 * n * n * x["col_degrees_lowp"] for x in last)
+    achieved = filt_flops / (filt_ms / 1e3) / 1e12 if filt_ms > 0 else 0.0
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    if prec == L.PREC_FP64:
+        roof = {"bound": "alu", "achieved": achieved, "peak": 1.10, "unit": "TFLOP/s",
+                "frac": achieved / 1.10, "traffic": None,
+                "kernel": "zgemm_nn_kernel (FP64 filter step, fused recurrence)",
+                "peak_source": "measured FP64 GEMM rate on this GB300 (torch float64 "
+                               "matmul, 8192^3), no FP64 figure in MEASURED_PEAKS.json"}
+    else:
+        pk = peaks.get("bf16_tflops_sustained", 1700.0)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                "frac": achieved / pk, "traffic": None,
+                "kernel": "filter steps (split-precision tcgen05 + FP64 sweeps)",
+                "peak_source": "bf16_tflops_sustained of measured"}
+
+    # end to end: same solve through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        Hh = [h.cpu().pin_memory() for h in Hcs]
+        X0h = X0c.cpu().pin_memory()
+        Xh = X0h.clone().pin_memory()
+        torch.cuda.synchronize()
+        reps = max(1, min(args.steps, 2))
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            Xh.copy_(X0h)
+            s.solve_sequence_host(Hh, nev, nex, Xh, cfg.tol)
+        t1 = time.perf_counter()
+        e2e = {"value": (t1 - t0) / reps / (length * ws), "unit": UNIT,
+               "h2d_bytes_per_step": int(length * 16 * n * n + 16 * n * k),
+               "d2h_bytes_per_step": int(16 * n * k + 8 * length * k)}
+
+    fp64_cmp = None
+    if args.fp64_compare and prec != L.PREC_FP64:
+        s64 = Chfsi(precision=L.PREC_FP64)
+        m = args.fp64_compare
+        Xc = X0c.clone()
+        s64.solve_sequence(Hcs[:m], nev, nex, Xc, cfg.tol)
+        torch.cuda.synchronize()
+        Xc = X0c.clone()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, sts64, _ = s64.solve_sequence(Hcs[:m], nev, nex, Xc, cfg.tol)
+        b.record(stream)
+        torch.cuda.synchronize()
+        fp64_cmp = {"s_per_problem": a.elapsed_time(b) / 1e3 / m, "problems": m}
+        s64.close()
+
+    cpu = None
+    if rank == 0 and ws == 1:
+        Hh2 = [Hcs[0].t().cpu().numpy(), Hcs[1].t().cpu().numpy()]
+        cpu = cpu_baseline_sample(Hh2, nev, nex, cfg.tol, X0, length)
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": sec_per_problem, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == L.PREC_FP64 else "bf16x3+f64",
+            "data": "synthetic",
+            "config": {"workload": f"correlated sequence of {length} complex128 Hermitian "
+                                   f"problems, n={n}, nev={nev}, nex={nex}, eps=1e-3, "
+                                   f"delta=1e-4, tol 1e-10",
+                       "precision": args.precision, "degree_model": "analytic",
+                       "l2": "inputs larger than L2 (each H is 16 n^2 bytes)",
+                       "parallelism": f"replicas x{ws}"},
+            "filter_tflops": achieved,
+            "filter_tflops_lowp_share": lowp_flops / filt_flops if filt_flops else 0.0,
+            "max_resid": max_res,
+            "loops": [x["loops"] for x in last],
+            "phase_ms": {p: sum(x["ms_" + p] for x in last)
+                         for p in ["lanczos", "filter", "qr", "rr", "resid", "lock"]},
+            "roofline": roof,
+            "gpu_launches": int(launches),
+            "filter_launches_per_step": int(filt_launch),
+            "clocks": ck,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "fp64_gpu": fp64_cmp,
+        }
+        print(json.dumps(out))
+    s.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

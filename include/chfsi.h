@@ -1,0 +1,219 @@
+/*
+ * chfsi.h -- C ABI of the GB300 ChFSI library (libchfsi.so).
+ *
+ * Chebyshev Filtered Subspace Iteration for sequences of correlated dense
+ * Hermitian eigenproblems, after Berljafa, Wortmann and Di Napoli, "An
+ * Optimized and Scalable Eigensolver for Sequences of Eigenvalue Problems"
+ * (arXiv 1404.4161): Algorithm 1 (ChFSI), Algorithm 2 (the Chebyshev filter
+ * with per-vector degrees), Sec. 3.2 (degree optimisation).
+ *
+ * Conventions for every entry point:
+ *  - Complex numbers are complex128 stored as interleaved (re, im) doubles.
+ *    A "complex n x k matrix" is n*k such pairs, column-major, leading
+ *    dimension n (column j starts at element j*n).
+ *  - Pointers are DEVICE pointers unless the parameter name ends in _host.
+ *    The caller owns every buffer it passes; the library never frees or
+ *    keeps a caller pointer beyond the call.
+ *  - Work is issued on the stream given to chfsi_init (a cudaStream_t passed
+ *    as void*; NULL = the legacy default stream).  Entry points that return
+ *    host-visible results (stats, *_host outputs) synchronise that stream
+ *    before returning; the others are stream-ordered.
+ *  - Return value: CHFSI_OK or one of the error codes below.  No entry point
+ *    exits the process or traps on the device.  chfsi_strerror() names a
+ *    code; chfsi_last_error() gives a message for the last failure on ctx.
+ *  - Not thread-safe per context: one host thread per chfsi_ctx at a time.
+ */
+#ifndef CHFSI_H
+#define CHFSI_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CHFSI_OK 0
+#define CHFSI_EINVAL 1      /* bad argument: sizes, NULL pointer, options  */
+#define CHFSI_ENOMEM 2      /* device allocation failed                     */
+#define CHFSI_ENOCONV 3     /* max_loops reached before nev pairs converged */
+#define CHFSI_EBREAKDOWN 4  /* QR breakdown: filtered block rank-deficient  */
+#define CHFSI_ENAN 5        /* NaN or Inf met in a reduction                */
+#define CHFSI_ETIMEOUT 6    /* a bounded device wait gave up                */
+#define CHFSI_ECUDA 7       /* CUDA / cuSOLVER runtime error                */
+#define CHFSI_ENOTSUP 8     /* configuration not supported on this device   */
+
+/* Arithmetic of the filter (the other steps always run in FP64). */
+#define CHFSI_PREC_FP64 0   /* complex FP64 filter on the FP64 pipe          */
+#define CHFSI_PREC_MIXED 1  /* split-precision tensor-core filter while the  */
+                            /* largest wanted residual > switch_tol, then    */
+                            /* FP64 filter sweeps to tol                     */
+
+/* Split format of the tensor-core filter (CHFSI_PREC_MIXED). */
+#define CHFSI_SPLIT_BF16X3 0 /* x = hi + lo in bf16; hi*hi + hi*lo + lo*hi   */
+#define CHFSI_SPLIT_FP16X3 1 /* same with fp16 and a power-of-two scaling    */
+
+/* Degree model (Alg. 1 line 11). */
+#define CHFSI_DEG_ANALYTIC 0 /* Single Optimization rule of Sec. 3.2         */
+#define CHFSI_DEG_MLP 1      /* learned predictor; analytic rule as fallback */
+
+typedef struct chfsi_ctx chfsi_ctx;
+
+typedef struct chfsi_opts {
+  int precision;       /* CHFSI_PREC_*                        (FP64)       */
+  int split;           /* CHFSI_SPLIT_*                       (BF16X3)     */
+  int degree_model;    /* CHFSI_DEG_*                         (ANALYTIC)   */
+  int deg_cold;        /* first-loop degree, random start     (20)         */
+  int deg_warm;        /* first-loop degree, warm start       (8)          */
+  int deg_min;         /* lower clamp of the degree rule      (1)          */
+  int deg_max;         /* upper clamp of the degree rule      (36)         */
+  int deg_extra;       /* margin added to the rule's ceiling  (1)          */
+  int lanczos_steps;   /* Lanczos steps for the bounds        (20)         */
+  int max_loops;       /* outer-loop limit                    (50)         */
+  double switch_tol;   /* MIXED: residual below which FP64 takes over (1e-4) */
+  unsigned long long seed; /* SplitMix64 seed of the Lanczos start (1)     */
+} chfsi_opts;
+
+/* Per-problem statistics (host struct, filled when non-NULL). */
+typedef struct chfsi_stats {
+  int status;               /* return code of this problem               */
+  int loops;                /* outer loops (filter + QR + RR)            */
+  int loops_lowp;           /* loops whose filter ran split-precision    */
+  int n_locked;             /* converged pairs at exit                   */
+  long long col_degrees;    /* sum over loops of sum_j m_j               */
+  long long col_degrees_lowp; /* the part done by the tensor-core filter */
+  double beta;              /* Lanczos upper bound of the spectrum       */
+  double norm_h;            /* ||H||_est used to normalise residuals     */
+  double max_resid;         /* largest residual of the nev wanted pairs  */
+  double ms_total;          /* wall time of the solve on the stream      */
+  double ms_lanczos, ms_filter, ms_qr, ms_rr, ms_resid, ms_lock;
+  double filter_flops;      /* useful filter flops, 8 n^2 sum m_j        */
+  long long filter_launches; /* filter-step kernel launches              */
+  long long launches;       /* all kernel launches of this solve         */
+} chfsi_stats;
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Fill *opts with the defaults shown above. */
+void chfsi_default_opts(chfsi_opts* opts);
+
+/* Create a context bound to the current CUDA device and `stream`.
+ * opts may be NULL (defaults).  Workspaces are allocated lazily and grown
+ * on demand; they belong to the context.  Returns EINVAL, ENOMEM, ECUDA or
+ * ENOTSUP (device is not sm_103 when the MIXED path is asked for). */
+int chfsi_init(chfsi_ctx** ctx, const chfsi_opts* opts, void* stream);
+
+/* Replace the options of an existing context (same validation as init). */
+int chfsi_set_opts(chfsi_ctx* ctx, const chfsi_opts* opts);
+
+/* Release the context and all its device memory.  NULL is ignored. */
+void chfsi_free(chfsi_ctx* ctx);
+
+const char* chfsi_strerror(int code);
+const char* chfsi_last_error(const chfsi_ctx* ctx);
+
+/* ---- the solver (Alg. 1) ---------------------------------------------- */
+
+/* Solve one problem: the nev lowest eigenpairs of the Hermitian H
+ * (Alg. 1; Alg. 2 for the filter).
+ *  H      complex n x n, Hermitian, read only (shift and scale of Alg. 2
+ *         line 1 are folded into the filter; H is never written).
+ *  X      complex n x (nev+nex); in: starting block X0, out: the block of
+ *         Ritz vectors, the locked (converged) pairs first, ascending.
+ *  evals  n_ev = nev+nex doubles (device), ascending within the locked part
+ *         and within the rest, matching X's columns.
+ *  warm_host  NULL for a random start, else two doubles {lam_1, lam_k} of
+ *         the previous problem (Alg. 1 Require line): gamma and alpha.
+ *  Requires 1 <= nev, 1 <= nex, nev + nex <= n.  On ENOCONV / EBREAKDOWN X
+ *  holds the last orthonormal iterate. */
+int chfsi_solve(chfsi_ctx* ctx, const double* H, int n, int nev, int nex,
+                double* X, double tol, double* evals,
+                const double* warm_host, chfsi_stats* stats_host);
+
+/* Solve a correlated sequence (Definitions 1-2, Sec. 2.2): problem l+1
+ * starts from problem l's Ritz vectors and its lam_1, lam_k.
+ *  H      array of N device pointers to complex n x n Hermitian matrices
+ *         (the array itself is in host memory).
+ *  X      in: X0 for the first problem; out: the Ritz vectors of the last.
+ *  evals  N x (nev+nex) doubles (device), row l = problem l.
+ *  stats_host  NULL or N structs. */
+int chfsi_solve_sequence(chfsi_ctx* ctx, const double* const* H_host, int N,
+                         int n, int nev, int nex, double* X, double tol,
+                         double* evals, chfsi_stats* stats_host);
+
+/* Same as chfsi_solve_sequence with every buffer in HOST memory: the call
+ * copies each H to the device (double-buffered against the solve of the
+ * previous problem), X in and out, and evals out. */
+int chfsi_solve_sequence_host(chfsi_ctx* ctx, const double* const* H_host, int N,
+                              int n, int nev, int nex, double* X_host, double tol,
+                              double* evals_host, chfsi_stats* stats_host);
+
+/* ---- the steps of the hot path, one entry point each ------------------ */
+
+/* Alg. 1 line 3: s-step Lanczos with full reorthogonalisation from the
+ * SplitMix64 start vector of `seed` (entry j = u(2j) + i u(2j+1), u(t) =
+ * 2 (splitmix64_t >> 11) 2^-53 - 1).  out_host[0..3] = {beta = theta_max +
+ * ||f||, theta_min, theta_max, ||H||_est = max(|theta_min|, |theta_max|)}. */
+int chfsi_lanczos(chfsi_ctx* ctx, const double* H, int n, int steps,
+                  unsigned long long seed, double* out_host);
+
+/* Alg. 2: filter the k columns of Y0 (complex n x k) with degrees
+ * degrees_host[0..k-1] (>= 1, ascending), Y_m,j = C_{m_j}(Hs) Y0_j /
+ * C_{m_j}(gamma_hat), Hs = (H - cI)/e, gamma_hat = (lam1 - c)/e.  Result in
+ * Y (complex n x k; may not alias Y0).  precision = CHFSI_PREC_FP64 or
+ * CHFSI_PREC_MIXED (tensor-core split product with the context's split
+ * format). */
+int chfsi_filter(chfsi_ctx* ctx, const double* H, int n, int k, const double* Y0,
+                 const int* degrees_host, double lam1, double c, double e,
+                 double* Y, int precision);
+
+/* Alg. 1 line 6: orthonormalise the k columns of Y (complex n x k, in
+ * place) against the nl orthonormal columns of L (complex n x nl; may be
+ * NULL when nl = 0) by two block Gram-Schmidt passes and CholQR2 (shifted
+ * CholQR3 when the Gram matrix is not numerically positive definite).
+ * The result is the unique Q with R's diagonal real positive.  EBREAKDOWN if
+ * the block is rank-deficient. */
+int chfsi_orthonormalize(chfsi_ctx* ctx, int n, int nl, const double* L, int k,
+                         double* Y);
+
+/* Alg. 1 lines 7-9: Rayleigh-Ritz on orthonormal Q (complex n x k):
+ * Z = HQ, G = Q^H Z (Hermitianised), G W = W Lambda, Y = QW, HY = ZW.
+ * Y and HY: complex n x k outputs; evals: k doubles, ascending. */
+int chfsi_rayleigh_ritz(chfsi_ctx* ctx, const double* H, int n, int k,
+                        const double* Q, double* Y, double* HY, double* evals);
+
+/* Residuals r_j = ||HY_j - evals_j Y_j||_2 / norm_h (k doubles out). */
+int chfsi_residuals(chfsi_ctx* ctx, int n, int k, const double* HY,
+                    const double* Y, const double* evals, double norm_h,
+                    double* resid);
+
+/* Sec. 3.2 Single Optimization: m_j = ceil(ln(r_j/tol)/acosh|t_j|) +
+ * deg_extra, t_j = (ritz_j - c)/e, clamped to [deg_min, deg_max], deg_max
+ * when |t_j| <= 1; columns j >= n_wanted are capped at the largest wanted
+ * degree.  ritz, resid: k doubles; degrees: k ints (all device). */
+int chfsi_degrees(chfsi_ctx* ctx, int k, const double* ritz, const double* resid,
+                  double c, double e, double tol, int n_wanted, int* degrees);
+
+/* ---- learned degree predictor (not in the paper) ---------------------- */
+
+/* The network: 5 features -> 64 tanh -> 64 tanh -> 1 linear, weights
+ * kept in the context as FP32 masters with FP16 copies for the products
+ * (FP32 accumulation).  Parameter vector layout (CHFSI_MLP_NPARAM floats):
+ * W1[64][5], b1[64], W2[64][64], b2[64], W3[64], b3[1]. */
+#define CHFSI_MLP_NPARAM (64 * 5 + 64 + 64 * 64 + 64 + 64 + 1)
+
+/* Copy parameters host -> context (resets the optimiser state) / out. */
+int chfsi_mlp_set_params(chfsi_ctx* ctx, const float* params_host);
+int chfsi_mlp_get_params(chfsi_ctx* ctx, float* params_host);
+
+/* Forward pass: x (B x 5 floats, row-major, device) -> y (B floats). */
+int chfsi_mlp_forward(chfsi_ctx* ctx, int B, const float* x, float* y);
+
+/* One training step on a batch: loss = 0.5 mean((y - target)^2), gradients
+ * by the backward kernels, then Adam (lr, beta1 0.9, beta2 0.999, eps
+ * 1e-8).  grads (CHFSI_MLP_NPARAM floats, device) may be NULL; loss_host
+ * may be NULL. */
+int chfsi_mlp_train_step(chfsi_ctx* ctx, int B, const float* x, const float* target,
+                         float lr, float* grads, float* loss_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHFSI_H */

@@ -1,0 +1,811 @@
+// C ABI and solver core of the ChFSI library.
+//
+// Host-side orchestration of Algorithm 1 (ChFSI) of arXiv 1404.4161 over
+// device kernels: Lanczos bounds (line 3), the Chebyshev filter of
+// Algorithm 2 (line 5), orthonormalisation against the locked block (line
+// 6), Rayleigh-Ritz (lines 7-9), residuals, locking (line 10) and degree
+// optimisation (line 11).  Every arithmetic step runs in this library's
+// kernels; the k x k Cholesky, triangular inverse and Hermitian
+// eigensolve of the reduced problems use cuSOLVER.  The host only reads a
+// small control block per loop (converged count, interval, sorted degrees)
+// to size the next launches.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <vector>
+
+#include "common.cuh"
+
+#include <atomic>
+
+static std::atomic<long long> g_launches{0};
+long long chfsi_launch_counter() { return g_launches.load(std::memory_order_relaxed); }
+void chfsi_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ===================================================== workspace & ctx ====
+void* ws_get(chfsi_ctx* ctx, const char* name, size_t bytes) {
+  DevBuf& b = ctx->ws[name];
+  if (bytes == 0) bytes = 16;
+  if (b.bytes < bytes) {
+    if (b.p) CHFSI_CUDA_TRY(cudaFree(b.p));
+    b.p = nullptr;
+    b.bytes = 0;
+    const size_t want = (bytes + 255) / 256 * 256;
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      b.p = nullptr;
+      throw ChfsiError{CHFSI_ENOMEM, std::string("cudaMalloc(") + name + ", " +
+                                         std::to_string(want) + " B) failed"};
+    }
+    b.bytes = want;
+  }
+  return b.p;
+}
+
+void ws_free_all(chfsi_ctx* ctx) {
+  for (auto& kv : ctx->ws)
+    if (kv.second.p) cudaFree(kv.second.p);
+  ctx->ws.clear();
+}
+
+void* pinned_get(chfsi_ctx* ctx, size_t bytes) {
+  if (ctx->pinned_bytes < bytes) {
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    ctx->pinned = nullptr;
+    ctx->pinned_bytes = 0;
+    const size_t want = std::max<size_t>(bytes, 1 << 16);
+    CHFSI_CUDA_TRY(cudaHostAlloc(&ctx->pinned, want, cudaHostAllocDefault));
+    ctx->pinned_bytes = want;
+  }
+  return ctx->pinned;
+}
+
+namespace {
+
+int run_guarded(chfsi_ctx* ctx, const std::function<void()>& body);
+
+void validate_opts(const chfsi_opts& o) {
+  CHFSI_REQUIRE(o.precision == CHFSI_PREC_FP64 || o.precision == CHFSI_PREC_MIXED,
+                "opts.precision");
+  CHFSI_REQUIRE(o.split == CHFSI_SPLIT_BF16X3 || o.split == CHFSI_SPLIT_FP16X3, "opts.split");
+  CHFSI_REQUIRE(o.degree_model == CHFSI_DEG_ANALYTIC || o.degree_model == CHFSI_DEG_MLP,
+                "opts.degree_model");
+  CHFSI_REQUIRE(o.deg_min >= 1 && o.deg_max >= o.deg_min && o.deg_max <= 512,
+                "opts.deg_min/deg_max");
+  CHFSI_REQUIRE(o.deg_cold >= 1 && o.deg_warm >= 1, "opts.deg_cold/deg_warm");
+  CHFSI_REQUIRE(o.deg_extra >= 0, "opts.deg_extra");
+  CHFSI_REQUIRE(o.lanczos_steps >= 2 && o.lanczos_steps <= 200, "opts.lanczos_steps");
+  CHFSI_REQUIRE(o.max_loops >= 1, "opts.max_loops");
+  CHFSI_REQUIRE(o.switch_tol > 0.0, "opts.switch_tol");
+}
+
+inline double2* C2(double* p) { return reinterpret_cast<double2*>(p); }
+inline const double2* C2(const double* p) { return reinterpret_cast<const double2*>(p); }
+
+// ------------------------------------------------------------ Lanczos ----
+// out4_dev = {beta, theta_min, theta_max, norm_h} (device).
+void lanczos_dev(chfsi_ctx* ctx, const double2* H, int n, int steps,
+                 unsigned long long seed, double* out4_dev) {
+  cudaStream_t st = ctx->stream;
+  const int m = std::min(steps, n);
+  double2* V = (double2*)ws_get(ctx, "lz_V", sizeof(double2) * (size_t)n * (m + 1));
+  double2* w = (double2*)ws_get(ctx, "lz_w", sizeof(double2) * (size_t)n);
+  double2* h1 = (double2*)ws_get(ctx, "lz_h1", sizeof(double2) * (m + 1));
+  double2* h2 = (double2*)ws_get(ctx, "lz_h2", sizeof(double2) * (m + 1));
+  double* ab = (double*)ws_get(ctx, "lz_ab", sizeof(double) * (2 * m + 2));
+  double* a = ab;
+  double* b = ab + m + 1;
+  lanczos_start_vec(st, n, seed, w);
+  vec_norm(st, n, w, b + m);
+  vec_scale_inv(st, n, w, b + m, V);
+  for (int j = 0; j < m; ++j) {
+    zhemv_cols(st, n, H, V + (size_t)j * n, w);
+    const double2* hh[2] = {h1, h2};
+    for (int pass = 0; pass < 2; ++pass) {
+      double2* h = const_cast<double2*>(hh[pass]);
+      zgemm_cn(ctx, j + 1, 1, n, V, n, w, n, h, j + 1);
+      EpiNN ep;
+      ep.alpha = -1.0;
+      ep.beta = 1.0;
+      ep.P = w;
+      ep.ldp = n;
+      ep.D = w;
+      ep.ldd = n;
+      zgemm_nn(st, n, 1, j + 1, V, n, h, j + 1, ep);
+    }
+    lanczos_alpha(st, j, h1, h2, a);
+    vec_norm(st, n, w, b + j);
+    vec_scale_inv(st, n, w, b + j, V + (size_t)(j + 1) * n);
+  }
+  tridiag_bounds(st, m, a, b, out4_dev);
+}
+
+// ------------------------------------------------------- FP64 filter ----
+void filter_f64(chfsi_ctx* ctx, const double2* H, int n, int k, const double2* Y0,
+                const int* deg, double lam1, double c, double e, double2* Yout) {
+  cudaStream_t st = ctx->stream;
+  const size_t blk = sizeof(double2) * (size_t)n * k;
+  double2* F[3] = {(double2*)ws_get(ctx, "flt0", blk), (double2*)ws_get(ctx, "flt1", blk),
+                   (double2*)ws_get(ctx, "flt2", blk)};
+  auto buf = [&](int i) -> const double2* { return i == 0 ? Y0 : F[i % 3]; };
+  const int mk = deg[k - 1];
+  const double sigma1 = e / (lam1 - c);
+  int s = (int)(std::upper_bound(deg, deg + k, 1) - deg);
+  {
+    EpiNN ep;
+    ep.alpha = sigma1 / e;
+    ep.shift = c;
+    ep.S = Y0;
+    ep.lds = n;
+    ep.D = F[1];
+    ep.ldd = n;
+    ep.F = Yout;
+    ep.ldf = n;
+    ep.fin_end = s;
+    zgemm_nn(st, n, k, n, H, n, Y0, n, ep);
+  }
+  double sigma = sigma1;
+  for (int i = 1; i < mk; ++i) {
+    const double sn = 1.0 / (2.0 / sigma1 - sigma);
+    const int s_new = (int)(std::upper_bound(deg, deg + k, i + 1) - deg);
+    const double2* cur = buf(i);
+    const double2* prev = buf(i - 1);
+    double2* nxt = F[(i + 1) % 3];
+    const size_t off = (size_t)s * n;
+    EpiNN ep;
+    ep.alpha = 2.0 * sn / e;
+    ep.shift = c;
+    ep.S = cur + off;
+    ep.lds = n;
+    ep.beta = -sn * sigma;
+    ep.P = prev + off;
+    ep.ldp = n;
+    ep.D = nxt + off;
+    ep.ldd = n;
+    ep.F = Yout + off;
+    ep.ldf = n;
+    ep.fin_end = s_new - s;
+    zgemm_nn(st, n, k - s, n, H, n, cur + off, n, ep);
+    sigma = sn;
+    s = s_new;
+  }
+}
+
+// ------------------------------------------------- cuSOLVER helpers ----
+int* dev_info(chfsi_ctx* ctx) { return (int*)ws_get(ctx, "solver_info", sizeof(int) * 4); }
+
+int read_info(chfsi_ctx* ctx) {
+  int* h = (int*)pinned_get(ctx, 64);
+  CHFSI_CUDA_TRY(cudaMemcpyAsync(h, dev_info(ctx), sizeof(int), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+  CHFSI_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return *h;
+}
+
+// Upper Cholesky factor of G (k x k) in place; returns LAPACK-style info.
+int potrf_upper(chfsi_ctx* ctx, int k, double2* G) {
+  int lwork = 0;
+  CHFSI_SOLVER_TRY(cusolverDnZpotrf_bufferSize(ctx->solver, CUBLAS_FILL_MODE_UPPER, k,
+                                               (cuDoubleComplex*)G, k, &lwork));
+  void* work = ws_get(ctx, "potrf_work", sizeof(cuDoubleComplex) * (size_t)std::max(lwork, 1));
+  CHFSI_SOLVER_TRY(cusolverDnZpotrf(ctx->solver, CUBLAS_FILL_MODE_UPPER, k,
+                                    (cuDoubleComplex*)G, k, (cuDoubleComplex*)work, lwork,
+                                    dev_info(ctx)));
+  return read_info(ctx);
+}
+
+// Inverse of the upper triangular R (k x k) in place, strict lower part zeroed.
+void trtri_upper(chfsi_ctx* ctx, int k, double2* R) {
+  zero_strict_lower(ctx->stream, k, R, k);
+  size_t dbytes = 0, hbytes = 0;
+  CHFSI_SOLVER_TRY(cusolverDnXtrtri_bufferSize(ctx->solver, CUBLAS_FILL_MODE_UPPER,
+                                               CUBLAS_DIAG_NON_UNIT, k, CUDA_C_64F, R, k,
+                                               &dbytes, &hbytes));
+  void* dwork = ws_get(ctx, "trtri_work", std::max<size_t>(dbytes, 16));
+  std::vector<char> hwork(std::max<size_t>(hbytes, 16));
+  CHFSI_SOLVER_TRY(cusolverDnXtrtri(ctx->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT,
+                                    k, CUDA_C_64F, R, k, dwork, dbytes, hwork.data(), hbytes,
+                                    dev_info(ctx)));
+  const int info = read_info(ctx);
+  if (info != 0)
+    throw ChfsiError{CHFSI_EBREAKDOWN, "triangular inverse: singular R (info " +
+                                           std::to_string(info) + ")"};
+}
+
+// Hermitian eigensolve of G (k x k, lower part read): eigenvectors overwrite G.
+void heevd(chfsi_ctx* ctx, int k, double2* G, double* w) {
+  int lwork = 0;
+  CHFSI_SOLVER_TRY(cusolverDnZheevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR,
+                                               CUBLAS_FILL_MODE_LOWER, k, (cuDoubleComplex*)G,
+                                               k, w, &lwork));
+  void* work = ws_get(ctx, "heevd_work", sizeof(cuDoubleComplex) * (size_t)std::max(lwork, 1));
+  CHFSI_SOLVER_TRY(cusolverDnZheevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR,
+                                    CUBLAS_FILL_MODE_LOWER, k, (cuDoubleComplex*)G, k, w,
+                                    (cuDoubleComplex*)work, lwork, dev_info(ctx)));
+  const int info = read_info(ctx);
+  if (info != 0)
+    throw ChfsiError{CHFSI_ECUDA, "reduced eigensolve failed (info " + std::to_string(info) +
+                                      ")"};
+}
+
+// ------------------------------------------------- orthonormalisation ----
+// Alg. 1 line 6 on the device: two block Gram-Schmidt passes against the
+// locked block, column normalisation, then CholQR2 (a shifted Cholesky QR
+// pass first when the Gram matrix is not numerically positive definite).
+void orthonormalize_dev(chfsi_ctx* ctx, int n, int nl, const double2* L, int k, double2* Y) {
+  cudaStream_t st = ctx->stream;
+  if (k <= 0) return;
+  if (nl > 0) {
+    double2* P = (double2*)ws_get(ctx, "qr_P", sizeof(double2) * (size_t)nl * k);
+    for (int pass = 0; pass < 2; ++pass) {
+      zgemm_cn(ctx, nl, k, n, L, n, Y, n, P, nl);
+      EpiNN ep;
+      ep.alpha = -1.0;
+      ep.beta = 1.0;
+      ep.P = Y;
+      ep.ldp = n;
+      ep.D = Y;
+      ep.ldd = n;
+      zgemm_nn(st, n, k, nl, L, n, P, nl, ep);
+    }
+  }
+  double* cn = (double*)ws_get(ctx, "qr_cn", sizeof(double) * k);
+  column_norms(st, n, k, Y, n, cn);
+  scale_columns_inv(st, n, k, Y, n, cn);
+  double2* G = (double2*)ws_get(ctx, "qr_G", sizeof(double2) * (size_t)k * k);
+  double2* T = (double2*)ws_get(ctx, "qr_T", sizeof(double2) * (size_t)n * k);
+  double* shift = (double*)ws_get(ctx, "qr_shift", sizeof(double));
+  int passes = 2;
+  bool shifted = false;
+  for (int pass = 0; pass < passes; ++pass) {
+    zgemm_cn(ctx, k, k, n, Y, n, Y, n, G, k);
+    hermitianize(st, k, G, k);
+    if (shifted && pass == 0) {
+      cholqr_shift(st, n, k, G, k, shift);
+      add_diag(st, k, G, k, shift);
+    }
+    int info = potrf_upper(ctx, k, G);
+    if (info != 0) {
+      if (pass == 0 && !shifted) {
+        shifted = true;
+        passes = 3;
+        pass = -1;  // restart with the shifted first pass
+        continue;
+      }
+      throw ChfsiError{CHFSI_EBREAKDOWN, "CholQR: Gram matrix not positive definite (info " +
+                                             std::to_string(info) + ")"};
+    }
+    trtri_upper(ctx, k, G);
+    EpiNN ep;
+    ep.D = T;
+    ep.ldd = n;
+    zgemm_nn(st, n, k, k, Y, n, G, k, ep);
+    CHFSI_CUDA_TRY(cudaMemcpyAsync(Y, T, sizeof(double2) * (size_t)n * k,
+                                   cudaMemcpyDeviceToDevice, st));
+  }
+}
+
+// ----------------------------------------------------- Rayleigh-Ritz ----
+void rayleigh_ritz_dev(chfsi_ctx* ctx, const double2* H, int n, int k, const double2* Q,
+                       double2* Y, double2* HY, double* evals) {
+  cudaStream_t st = ctx->stream;
+  double2* Z = (double2*)ws_get(ctx, "rr_Z", sizeof(double2) * (size_t)n * k);
+  double2* G = (double2*)ws_get(ctx, "rr_G", sizeof(double2) * (size_t)k * k);
+  {
+    EpiNN ep;
+    ep.D = Z;
+    ep.ldd = n;
+    zgemm_nn(st, n, k, n, H, n, Q, n, ep);
+  }
+  zgemm_cn(ctx, k, k, n, Q, n, Z, n, G, k);
+  hermitianize(st, k, G, k);
+  // The reduced eigensolver is iterative: never hand it NaN or Inf.
+  if (any_nonfinite(ctx, (size_t)2 * k * k, (const double*)G))
+    throw ChfsiError{CHFSI_ENAN, "NaN/Inf in the Rayleigh quotient"};
+  heevd(ctx, k, G, evals);
+  {
+    EpiNN ep;
+    ep.D = Y;
+    ep.ldd = n;
+    zgemm_nn(st, n, k, k, Q, n, G, k, ep);
+  }
+  {
+    EpiNN ep;
+    ep.D = HY;
+    ep.ldd = n;
+    zgemm_nn(st, n, k, k, Z, n, G, k, ep);
+  }
+}
+
+// ---------------------------------------------------------- timing -------
+struct PhaseTimer {
+  chfsi_ctx* ctx;
+  int cur = 0;
+  explicit PhaseTimer(chfsi_ctx* c) : ctx(c) {}
+  void mark(int i) { CHFSI_CUDA_TRY(cudaEventRecord(ctx->ev[i], ctx->stream)); }
+  double ms(int a, int b) {
+    float t = 0.f;
+    CHFSI_CUDA_TRY(cudaEventElapsedTime(&t, ctx->ev[a], ctx->ev[b]));
+    return (double)t;
+  }
+};
+
+// ------------------------------------------------------- solve one -------
+int solve_one(chfsi_ctx* ctx, const double2* H, int n, int nev, int nex, double2* X,
+              double tol, double* evals_out, const double* warm, chfsi_stats* stats) {
+  const chfsi_opts& o = ctx->opts;
+  cudaStream_t st = ctx->stream;
+  const int k = nev + nex;
+  CHFSI_REQUIRE(H && X && evals_out, "NULL buffer");
+  CHFSI_REQUIRE(nev >= 1 && nex >= 1 && k <= n, "need 1 <= nev, 1 <= nex, nev + nex <= n");
+  CHFSI_REQUIRE(tol > 0.0, "tol must be > 0");
+  const bool mixed = o.precision == CHFSI_PREC_MIXED;
+  if (mixed && !tc_filter_supported(ctx))
+    throw ChfsiError{CHFSI_ENOTSUP, "split-precision filter needs an sm_103 device"};
+
+  chfsi_stats S;
+  std::memset(&S, 0, sizeof(S));
+  const long long launches0 = chfsi_launch_counter();
+  PhaseTimer tm(ctx);
+  tm.mark(0);
+
+  const size_t blk = sizeof(double2) * (size_t)n * k;
+  double2* Xact = (double2*)ws_get(ctx, "s_Xact", blk);
+  double2* Yf = (double2*)ws_get(ctx, "s_Yf", blk);
+  double2* Yrr = (double2*)ws_get(ctx, "s_Yrr", blk);
+  double2* HY = (double2*)ws_get(ctx, "s_HY", blk);
+  double2* Lk = (double2*)ws_get(ctx, "s_Lk", sizeof(double2) * (size_t)n * nev);
+  double* lam = (double*)ws_get(ctx, "s_lam", sizeof(double) * k);
+  double* res = (double*)ws_get(ctx, "s_res", sizeof(double) * k);
+  double* lamL = (double*)ws_get(ctx, "s_lamL", sizeof(double) * nev);
+  double* resL = (double*)ws_get(ctx, "s_resL", sizeof(double) * nev);
+  int* iws = (int*)ws_get(ctx, "s_int", sizeof(int) * 5 * (size_t)k);
+  int* lock_idx = iws;
+  int* act_idx = iws + k;
+  int* deg = iws + 2 * k;
+  int* perm = iws + 3 * k;
+  int* deg_sorted = iws + 4 * k;
+  double* bnd = (double*)ws_get(ctx, "s_bnd", sizeof(double) * 4);
+  LoopCtl* ctl = (LoopCtl*)ws_get(ctx, "s_ctl", sizeof(LoopCtl));
+  char* hp = (char*)pinned_get(ctx, 1024 + sizeof(int) * (size_t)k + sizeof(double) * k);
+  LoopCtl* ctl_h = (LoopCtl*)(hp + 256);
+  double* bnd_h = (double*)(hp + 512);
+  int* deg_h = (int*)(hp + 1024);
+
+  if (any_nonfinite(ctx, (size_t)2 * n * k, (const double*)X))
+    throw ChfsiError{CHFSI_ENAN, "NaN/Inf in the starting block"};
+  if (any_nonfinite(ctx, (size_t)2 * n * n, (const double*)H))
+    throw ChfsiError{CHFSI_ENAN, "NaN/Inf in H"};
+  // Alg. 1 line 3: bounds of the spectrum.
+  lanczos_dev(ctx, H, n, o.lanczos_steps, o.seed, bnd);
+  CHFSI_CUDA_TRY(cudaMemcpyAsync(bnd_h, bnd, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
+  tm.mark(1);
+  CHFSI_CUDA_TRY(cudaStreamSynchronize(st));
+  S.ms_lanczos = tm.ms(0, 1);
+  const double beta = bnd_h[0];
+  const double norm_h = bnd_h[3];
+  if (!std::isfinite(beta) || !std::isfinite(norm_h) || norm_h <= 0.0)
+    throw ChfsiError{CHFSI_ENAN, "Lanczos bounds are not finite"};
+  S.beta = beta;
+  S.norm_h = norm_h;
+  double alpha, gamma;
+  int deg0;
+  if (warm) {
+    gamma = warm[0];
+    alpha = warm[1];
+    deg0 = o.deg_warm;
+  } else {
+    gamma = bnd_h[1];
+    alpha = gamma + (beta - gamma) * (double)k / (double)n;
+    deg0 = o.deg_cold;
+  }
+  CHFSI_REQUIRE(alpha < beta, "filter interval is empty (alpha >= beta)");
+
+  copy_columns(st, n, k, X, n, Xact, n);
+  std::vector<int> degs(k, deg0);
+  int ka = k, nl = 0;
+  double max_resid_wanted = INFINITY;
+  bool lowp_on = mixed;
+  int status = CHFSI_ENOCONV;
+  int loops = 0;
+  while (loops < o.max_loops) {
+    ++loops;
+    const double c = 0.5 * (alpha + beta), e = 0.5 * (beta - alpha);
+    if (lowp_on && !(max_resid_wanted > o.switch_tol)) lowp_on = false;
+    long long sdeg = 0;
+    for (int j = 0; j < ka; ++j) sdeg += degs[j];
+    tm.mark(2);
+    const long long fl0 = chfsi_launch_counter();
+    if (lowp_on) {
+      tc_filter_run(ctx, H, n, ka, Xact, degs.data(), gamma, c, e, Yf);
+      S.loops_lowp++;
+      S.col_degrees_lowp += sdeg;
+    } else {
+      filter_f64(ctx, H, n, ka, Xact, degs.data(), gamma, c, e, Yf);
+    }
+    S.col_degrees += sdeg;
+    S.filter_launches += chfsi_launch_counter() - fl0;
+    tm.mark(3);
+    orthonormalize_dev(ctx, n, nl, Lk, ka, Yf);
+    tm.mark(4);
+    rayleigh_ritz_dev(ctx, H, n, ka, Yf, Yrr, HY, lam);
+    tm.mark(5);
+    residual_norms(st, n, ka, HY, Yrr, lam, norm_h, res);
+    tm.mark(6);
+    lock_select(st, ka, lam, res, nev - nl, tol, gamma, ctl, lock_idx, act_idx);
+    CHFSI_CUDA_TRY(cudaMemcpyAsync(ctl_h, ctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, st));
+    CHFSI_CUDA_TRY(cudaStreamSynchronize(st));
+    if (ctl_h->nonfinite) throw ChfsiError{CHFSI_ENAN, "NaN/Inf in Ritz values or residuals"};
+    const int n_new = ctl_h->n_new_locked;
+    gather_columns(st, n, n_new, Yrr, n, lock_idx, Lk + (size_t)nl * n, n);
+    gather_values(st, n_new, lam, lock_idx, lamL + nl);
+    gather_values(st, n_new, res, lock_idx, resL + nl);
+    nl += n_new;
+    ka = ctl_h->k_active;
+    gamma = ctl_h->gamma;
+    max_resid_wanted = ctl_h->max_resid_wanted;
+    if (nl >= nev) {
+      status = CHFSI_OK;
+      tm.mark(7);
+      CHFSI_CUDA_TRY(cudaStreamSynchronize(st));
+    } else {
+      alpha = ctl_h->alpha;
+      const double c2 = 0.5 * (alpha + beta), e2 = 0.5 * (beta - alpha);
+      if (o.degree_model == CHFSI_DEG_MLP) {
+        mlp_degrees(ctx, ka, lam, res, act_idx, c2, e2, gamma, 0, deg);
+        degree_cap_buffer(st, ka, nev - nl, deg);
+      } else {
+        degrees_analytic(st, ka, lam, res, act_idx, c2, e2, tol, nev - nl, o.deg_min,
+                         o.deg_max, o.deg_extra, deg);
+      }
+      sort_by_degree(st, ka, deg, act_idx, perm, deg_sorted);
+      gather_columns(st, n, ka, Yrr, n, perm, Xact, n);
+      CHFSI_CUDA_TRY(cudaMemcpyAsync(deg_h, deg_sorted, sizeof(int) * ka,
+                                     cudaMemcpyDeviceToHost, st));
+      tm.mark(7);
+      CHFSI_CUDA_TRY(cudaStreamSynchronize(st));
+      degs.assign(deg_h, deg_h + ka);
+    }
+    S.ms_filter += tm.ms(2, 3);
+    S.ms_qr += tm.ms(3, 4);
+    S.ms_rr += tm.ms(4, 5);
+    S.ms_resid += tm.ms(5, 6);
+    S.ms_lock += tm.ms(6, 7);
+    if (status == CHFSI_OK) break;
+  }
+  // Output: locked pairs ascending, then the remaining active block.
+  int* permL = perm;
+  sort_by_value(st, nl, lamL, permL);
+  gather_columns(st, n, nl, Lk, n, permL, X, n);
+  gather_values(st, nl, lamL, permL, evals_out);
+  gather_columns(st, n, ka, Yrr, n, act_idx, X + (size_t)nl * n, n);
+  gather_values(st, ka, lam, act_idx, evals_out + nl);
+  double* rl_h = (double*)(hp + 1024);
+  CHFSI_CUDA_TRY(cudaMemcpyAsync(rl_h, resL, sizeof(double) * std::max(nl, 1),
+                                 cudaMemcpyDeviceToHost, st));
+  tm.mark(8);
+  CHFSI_CUDA_TRY(cudaStreamSynchronize(st));
+  double mr = 0.0;
+  for (int j = 0; j < std::min(nl, nev); ++j) mr = std::max(mr, rl_h[j]);
+  S.max_resid = (nl >= nev) ? mr : INFINITY;
+  S.loops = loops;
+  S.n_locked = nl;
+  S.status = status;
+  S.ms_total = tm.ms(0, 8);
+  S.filter_flops = 8.0 * (double)n * (double)n * (double)S.col_degrees;
+  S.launches = chfsi_launch_counter() - launches0;
+  if (stats) *stats = S;
+  return status;
+}
+
+int run_guarded(chfsi_ctx* ctx, const std::function<void()>& body) {
+  try {
+    body();
+    ctx->last_error.clear();
+    return CHFSI_OK;
+  } catch (const ChfsiError& e) {
+    ctx->last_error = e.msg;
+    return e.code;
+  } catch (const std::exception& e) {
+    ctx->last_error = e.what();
+    return CHFSI_ECUDA;
+  }
+}
+
+}  // namespace
+
+// ============================================================ C ABI =====
+extern "C" {
+
+void chfsi_default_opts(chfsi_opts* o) {
+  if (!o) return;
+  o->precision = CHFSI_PREC_FP64;
+  o->split = CHFSI_SPLIT_BF16X3;
+  o->degree_model = CHFSI_DEG_ANALYTIC;
+  o->deg_cold = 20;
+  o->deg_warm = 8;
+  o->deg_min = 1;
+  o->deg_max = 36;
+  o->deg_extra = 1;
+  o->lanczos_steps = 20;
+  o->max_loops = 50;
+  o->switch_tol = 1e-4;
+  o->seed = 1ull;
+}
+
+const char* chfsi_strerror(int code) {
+  switch (code) {
+    case CHFSI_OK: return "ok";
+    case CHFSI_EINVAL: return "invalid argument";
+    case CHFSI_ENOMEM: return "out of device memory";
+    case CHFSI_ENOCONV: return "not converged within max_loops";
+    case CHFSI_EBREAKDOWN: return "orthonormalisation breakdown (rank-deficient block)";
+    case CHFSI_ENAN: return "NaN or Inf encountered";
+    case CHFSI_ETIMEOUT: return "device wait timed out";
+    case CHFSI_ECUDA: return "CUDA runtime error";
+    case CHFSI_ENOTSUP: return "not supported on this device";
+    default: return "unknown error";
+  }
+}
+
+const char* chfsi_last_error(const chfsi_ctx* ctx) {
+  return ctx ? ctx->last_error.c_str() : "no context";
+}
+
+int chfsi_init(chfsi_ctx** out, const chfsi_opts* opts, void* stream) {
+  if (!out) return CHFSI_EINVAL;
+  *out = nullptr;
+  chfsi_ctx* ctx = new chfsi_ctx();
+  if (opts) ctx->opts = *opts; else chfsi_default_opts(&ctx->opts);
+  ctx->stream = (cudaStream_t)stream;
+  int rc = run_guarded(ctx, [&] {
+    validate_opts(ctx->opts);
+    CHFSI_CUDA_TRY(cudaGetDevice(&ctx->device));
+    cudaDeviceProp p;
+    CHFSI_CUDA_TRY(cudaGetDeviceProperties(&p, ctx->device));
+    ctx->sm_count = p.multiProcessorCount;
+    ctx->cc_major = p.major;
+    ctx->cc_minor = p.minor;
+    CHFSI_SOLVER_TRY(cusolverDnCreate(&ctx->solver));
+    CHFSI_SOLVER_TRY(cusolverDnSetStream(ctx->solver, ctx->stream));
+    for (auto& e : ctx->ev) CHFSI_CUDA_TRY(cudaEventCreate(&e));
+    if (ctx->opts.precision == CHFSI_PREC_MIXED && !tc_filter_supported(ctx))
+      throw ChfsiError{CHFSI_ENOTSUP, "split-precision filter needs an sm_103 device"};
+    mlp_create(ctx);
+  });
+  if (rc != CHFSI_OK) {
+    chfsi_free(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return CHFSI_OK;
+}
+
+int chfsi_set_opts(chfsi_ctx* ctx, const chfsi_opts* opts) {
+  if (!ctx || !opts) return CHFSI_EINVAL;
+  return run_guarded(ctx, [&] {
+    validate_opts(*opts);
+    if (opts->precision == CHFSI_PREC_MIXED && !tc_filter_supported(ctx))
+      throw ChfsiError{CHFSI_ENOTSUP, "split-precision filter needs an sm_103 device"};
+    ctx->opts = *opts;
+  });
+}
+
+void chfsi_free(chfsi_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  tc_filter_release(ctx);
+  mlp_destroy(ctx);
+  ws_free_all(ctx);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  for (auto& e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  if (ctx->solver) cusolverDnDestroy(ctx->solver);
+  delete ctx;
+}
+
+int chfsi_solve(chfsi_ctx* ctx, const double* H, int n, int nev, int nex, double* X,
+                double tol, double* evals, const double* warm_host, chfsi_stats* stats) {
+  if (!ctx) return CHFSI_EINVAL;
+  int status = CHFSI_OK;
+  int rc = run_guarded(ctx, [&] {
+    CHFSI_REQUIRE(n >= 1, "n must be >= 1");
+    status = solve_one(ctx, C2(H), n, nev, nex, C2(X), tol, evals, warm_host, stats);
+  });
+  if (rc != CHFSI_OK) {
+    if (stats) stats->status = rc;
+    return rc;
+  }
+  if (status == CHFSI_ENOCONV) ctx->last_error = "max_loops reached";
+  return status;
+}
+
+int chfsi_solve_sequence(chfsi_ctx* ctx, const double* const* H, int N, int n, int nev,
+                         int nex, double* X, double tol, double* evals, chfsi_stats* stats) {
+  if (!ctx) return CHFSI_EINVAL;
+  int status = CHFSI_OK;
+  int rc = run_guarded(ctx, [&] {
+    CHFSI_REQUIRE(H && N >= 1 && n >= 1, "bad sequence arguments");
+    const int k = nev + nex;
+    double warm[2];
+    double* wh = (double*)pinned_get(ctx, 1024 + sizeof(int) * (size_t)(k + 8) +
+                                              sizeof(double) * (size_t)(k + 8));
+    for (int l = 0; l < N; ++l) {
+      CHFSI_REQUIRE(H[l] != nullptr, "NULL H in sequence");
+      double* ev = evals + (size_t)l * k;
+      const int s = solve_one(ctx, C2(H[l]), n, nev, nex, C2(X), tol, ev, l ? warm : nullptr,
+                              stats ? stats + l : nullptr);
+      if (s != CHFSI_OK && status == CHFSI_OK) status = s;
+      CHFSI_CUDA_TRY(cudaMemcpyAsync(wh, ev, sizeof(double), cudaMemcpyDeviceToHost,
+                                     ctx->stream));
+      CHFSI_CUDA_TRY(cudaMemcpyAsync(wh + 1, ev + k - 1, sizeof(double),
+                                     cudaMemcpyDeviceToHost, ctx->stream));
+      CHFSI_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+      warm[0] = wh[0];
+      warm[1] = wh[1];
+    }
+  });
+  return rc != CHFSI_OK ? rc : status;
+}
+
+int chfsi_solve_sequence_host(chfsi_ctx* ctx, const double* const* H, int N, int n, int nev,
+                              int nex, double* X_host, double tol, double* evals_host,
+                              chfsi_stats* stats) {
+  if (!ctx) return CHFSI_EINVAL;
+  int status = CHFSI_OK;
+  int rc = run_guarded(ctx, [&] {
+    CHFSI_REQUIRE(H && N >= 1 && n >= 1 && X_host && evals_host, "bad sequence arguments");
+    const int k = nev + nex;
+    const size_t hb = sizeof(double2) * (size_t)n * n;
+    double* Hd[2] = {(double*)ws_get(ctx, "hs_H0", hb), (double*)ws_get(ctx, "hs_H1", hb)};
+    double* Xd = (double*)ws_get(ctx, "hs_X", sizeof(double2) * (size_t)n * k);
+    double* Ed = (double*)ws_get(ctx, "hs_E", sizeof(double) * (size_t)N * k);
+    CHFSI_CUDA_TRY(cudaMemcpyAsync(Xd, X_host, sizeof(double2) * (size_t)n * k,
+                                   cudaMemcpyHostToDevice, ctx->stream));
+    double warm[2];
+    double* wh = (double*)pinned_get(ctx, 1024 + sizeof(int) * (size_t)(k + 8) +
+                                              sizeof(double) * (size_t)(k + 8));
+    for (int l = 0; l < N; ++l) {
+      CHFSI_REQUIRE(H[l] != nullptr, "NULL H in sequence");
+      double* hd = Hd[l & 1];
+      CHFSI_CUDA_TRY(cudaMemcpyAsync(hd, H[l], hb, cudaMemcpyHostToDevice, ctx->stream));
+      double* ev = Ed + (size_t)l * k;
+      const int s = solve_one(ctx, C2((const double*)hd), n, nev, nex, C2(Xd), tol, ev,
+                              l ? warm : nullptr, stats ? stats + l : nullptr);
+      if (s != CHFSI_OK && status == CHFSI_OK) status = s;
+      CHFSI_CUDA_TRY(cudaMemcpyAsync(wh, ev, sizeof(double), cudaMemcpyDeviceToHost,
+                                     ctx->stream));
+      CHFSI_CUDA_TRY(cudaMemcpyAsync(wh + 1, ev + k - 1, sizeof(double),
+                                     cudaMemcpyDeviceToHost, ctx->stream));
+      CHFSI_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+      warm[0] = wh[0];
+      warm[1] = wh[1];
+    }
+    CHFSI_CUDA_TRY(cudaMemcpyAsync(X_host, Xd, sizeof(double2) * (size_t)n * k,
+                                   cudaMemcpyDeviceToHost, ctx->stream));
+    CHFSI_CUDA_TRY(cudaMemcpyAsync(evals_host, Ed, sizeof(double) * (size_t)N * k,
+                                   cudaMemcpyDeviceToHost, ctx->stream));
+    CHFSI_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  });
+  return rc != CHFSI_OK ? rc : status;
+}
+
+int chfsi_lanczos(chfsi_ctx* ctx, const double* H, int n, int steps, unsigned long long seed,
+                  double* out_host) {
+  if (!ctx) return CHFSI_EINVAL;
+  return run_guarded(ctx, [&] {
+    CHFSI_REQUIRE(H && out_host && n >= 1 && steps >= 2, "bad Lanczos arguments");
+    double* d = (double*)ws_get(ctx, "api_bnd", sizeof(double) * 4);
+    lanczos_dev(ctx, C2(H), n, steps, seed, d);
+    CHFSI_CUDA_TRY(cudaMemcpyAsync(out_host, d, sizeof(double) * 4, cudaMemcpyDeviceToHost,
+                                   ctx->stream));
+    CHFSI_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+int chfsi_filter(chfsi_ctx* ctx, const double* H, int n, int k, const double* Y0,
+                 const int* degrees_host, double lam1, double c, double e, double* Y,
+                 int precision) {
+  if (!ctx) return CHFSI_EINVAL;
+  return run_guarded(ctx, [&] {
+    CHFSI_REQUIRE(n >= 1 && k >= 0 && k <= n, "bad filter sizes");
+    if (k == 0) return;
+    CHFSI_REQUIRE(H && Y0 && Y && degrees_host && Y0 != Y, "bad filter buffers");
+    CHFSI_REQUIRE(e > 0.0 && lam1 != c, "bad filter interval");
+    for (int j = 0; j < k; ++j) {
+      CHFSI_REQUIRE(degrees_host[j] >= 1, "degrees must be >= 1");
+      CHFSI_REQUIRE(j == 0 || degrees_host[j] >= degrees_host[j - 1],
+                    "degrees must be ascending");
+    }
+    if (precision == CHFSI_PREC_MIXED) {
+      if (!tc_filter_supported(ctx))
+        throw ChfsiError{CHFSI_ENOTSUP, "split-precision filter needs an sm_103 device"};
+      tc_filter_run(ctx, C2(H), n, k, C2(Y0), degrees_host, lam1, c, e, C2(Y));
+    } else {
+      CHFSI_REQUIRE(precision == CHFSI_PREC_FP64, "bad precision");
+      filter_f64(ctx, C2(H), n, k, C2(Y0), degrees_host, lam1, c, e, C2(Y));
+    }
+  });
+}
+
+int chfsi_orthonormalize(chfsi_ctx* ctx, int n, int nl, const double* L, int k, double* Y) {
+  if (!ctx) return CHFSI_EINVAL;
+  return run_guarded(ctx, [&] {
+    CHFSI_REQUIRE(n >= 1 && nl >= 0 && k >= 0 && nl + k <= n, "bad QR sizes");
+    CHFSI_REQUIRE(Y && (nl == 0 || L), "bad QR buffers");
+    orthonormalize_dev(ctx, n, nl, C2(L), k, C2(Y));
+  });
+}
+
+int chfsi_rayleigh_ritz(chfsi_ctx* ctx, const double* H, int n, int k, const double* Q,
+                        double* Y, double* HY, double* evals) {
+  if (!ctx) return CHFSI_EINVAL;
+  return run_guarded(ctx, [&] {
+    CHFSI_REQUIRE(n >= 1 && k >= 1 && k <= n, "bad RR sizes");
+    CHFSI_REQUIRE(H && Q && Y && HY && evals, "bad RR buffers");
+    rayleigh_ritz_dev(ctx, C2(H), n, k, C2(Q), C2(Y), C2(HY), evals);
+  });
+}
+
+int chfsi_residuals(chfsi_ctx* ctx, int n, int k, const double* HY, const double* Y,
+                    const double* evals, double norm_h, double* resid) {
+  if (!ctx) return CHFSI_EINVAL;
+  return run_guarded(ctx, [&] {
+    CHFSI_REQUIRE(n >= 1 && k >= 0 && norm_h > 0.0, "bad residual arguments");
+    if (k == 0) return;
+    CHFSI_REQUIRE(HY && Y && evals && resid, "bad residual buffers");
+    residual_norms(ctx->stream, n, k, C2(HY), C2(Y), evals, norm_h, resid);
+  });
+}
+
+int chfsi_degrees(chfsi_ctx* ctx, int k, const double* ritz, const double* resid, double c,
+                  double e, double tol, int n_wanted, int* degrees) {
+  if (!ctx) return CHFSI_EINVAL;
+  return run_guarded(ctx, [&] {
+    CHFSI_REQUIRE(k >= 0 && e > 0.0 && tol > 0.0, "bad degree arguments");
+    if (k == 0) return;
+    CHFSI_REQUIRE(ritz && resid && degrees, "bad degree buffers");
+    const chfsi_opts& o = ctx->opts;
+    degrees_analytic(ctx->stream, k, ritz, resid, nullptr, c, e, tol, n_wanted, o.deg_min,
+                     o.deg_max, o.deg_extra, degrees);
+  });
+}
+
+int chfsi_mlp_set_params(chfsi_ctx* ctx, const float* params_host) {
+  if (!ctx || !params_host) return CHFSI_EINVAL;
+  return run_guarded(ctx, [&] { mlp_set_params(ctx, params_host); });
+}
+
+int chfsi_mlp_get_params(chfsi_ctx* ctx, float* params_host) {
+  if (!ctx || !params_host) return CHFSI_EINVAL;
+  return run_guarded(ctx, [&] { mlp_get_params(ctx, params_host); });
+}
+
+int chfsi_mlp_forward(chfsi_ctx* ctx, int B, const float* x, float* y) {
+  if (!ctx) return CHFSI_EINVAL;
+  return run_guarded(ctx, [&] {
+    CHFSI_REQUIRE(B >= 0, "bad batch");
+    if (B == 0) return;
+    CHFSI_REQUIRE(x && y, "bad MLP buffers");
+    mlp_forward(ctx, B, x, y);
+  });
+}
+
+int chfsi_mlp_train_step(chfsi_ctx* ctx, int B, const float* x, const float* target, float lr,
+                         float* grads, float* loss_host) {
+  if (!ctx) return CHFSI_EINVAL;
+  return run_guarded(ctx, [&] {
+    CHFSI_REQUIRE(B >= 1 && x && target && lr > 0.f, "bad MLP training arguments");
+    float* loss_dev = (float*)ws_get(ctx, "mlp_loss", sizeof(float));
+    mlp_train_step(ctx, B, x, target, lr, grads, loss_dev);
+    if (loss_host) {
+      CHFSI_CUDA_TRY(cudaMemcpyAsync(loss_host, loss_dev, sizeof(float), cudaMemcpyDeviceToHost,
+                                     ctx->stream));
+      CHFSI_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    }
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,187 @@
+// Shared definitions of the ChFSI CUDA library: the context, workspace
+// management, error plumbing and the launch wrappers each .cu file exports
+// to the solver core (api.cu).  Device code is sm_103a only.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/chfsi.h"
+
+// ---------------------------------------------------------------- errors --
+struct ChfsiError {
+  int code;
+  std::string msg;
+};
+
+#define CHFSI_CUDA_TRY(call)                                                   \
+  do {                                                                         \
+    cudaError_t e_ = (call);                                                   \
+    if (e_ != cudaSuccess)                                                     \
+      throw ChfsiError{CHFSI_ECUDA, std::string(#call) + ": " +                \
+                                        cudaGetErrorString(e_)};               \
+  } while (0)
+
+#define CHFSI_SOLVER_TRY(call)                                                 \
+  do {                                                                         \
+    cusolverStatus_t s_ = (call);                                              \
+    if (s_ != CUSOLVER_STATUS_SUCCESS)                                         \
+      throw ChfsiError{CHFSI_ECUDA,                                            \
+                       std::string(#call) + ": cusolver status " +             \
+                           std::to_string((int)s_)};                           \
+  } while (0)
+
+#define CHFSI_REQUIRE(cond, text)                                              \
+  do {                                                                         \
+    if (!(cond)) throw ChfsiError{CHFSI_EINVAL, text};                         \
+  } while (0)
+
+// Kernel launches issued by this library (all contexts, all threads).
+long long chfsi_launch_counter();
+void chfsi_count_launch();
+
+// Check the launch just issued (configuration errors only; asynchronous
+// faults surface at the next synchronising call) and count it.
+inline void chfsi_check_launch(const char* what) {
+  chfsi_count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess)
+    throw ChfsiError{CHFSI_ECUDA, std::string(what) + ": " + cudaGetErrorString(e)};
+}
+
+// ------------------------------------------------------------- context ----
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+// Tensor-core filter state kept per context (split copies of H and the
+// Y operand buffers); defined in filter_tc.cu.
+struct TcFilterState;
+
+struct MlpState;
+
+struct chfsi_ctx {
+  chfsi_opts opts;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sm_count = 0;
+  int cc_major = 0, cc_minor = 0;
+  cusolverDnHandle_t solver = nullptr;
+  std::string last_error;
+  std::unordered_map<std::string, DevBuf> ws;
+  void* pinned = nullptr;  // small page-locked control buffer
+  size_t pinned_bytes = 0;
+  TcFilterState* tc = nullptr;
+  MlpState* mlp = nullptr;
+  cudaEvent_t ev[16] = {};
+};
+
+// Device buffer named `name` with at least `bytes` bytes (grown on demand;
+// contents are not preserved when it grows).
+void* ws_get(chfsi_ctx* ctx, const char* name, size_t bytes);
+void ws_free_all(chfsi_ctx* ctx);
+void* pinned_get(chfsi_ctx* ctx, size_t bytes);
+
+// ------------------------------------------------- FP64 dense kernels ------
+// All complex matrices are double2 (re, im), column-major.
+
+// Epilogue of the NN product acc = A(M x K) B(K x N):
+//   v = alpha * (acc - shift * S) + beta * P;  D = v;  F = v for columns
+//   c < fin_end (F may be null).  S, P may be null when shift, beta are 0.
+// D may alias P (each element is read then written by one thread).
+struct EpiNN {
+  double alpha = 1.0, shift = 0.0, beta = 0.0;
+  const double2* S = nullptr;
+  int lds = 0;
+  const double2* P = nullptr;
+  int ldp = 0;
+  double2* D = nullptr;
+  int ldd = 0;
+  double2* F = nullptr;
+  int ldf = 0;
+  int fin_end = 0;
+};
+
+void zgemm_nn(cudaStream_t st, int M, int N, int K, const double2* A, int lda,
+              const double2* B, int ldb, const EpiNN& ep);
+
+// C (K1 x K2, ldc) = alpha * A^H B + beta * C, A: Nr x K1, B: Nr x K2 (split
+// over the long dimension Nr, partial sums reduced in a fixed order).
+void zgemm_cn(chfsi_ctx* ctx, int K1, int K2, int Nr, const double2* A, int lda,
+              const double2* B, int ldb, double2* C, int ldc, double alpha = 1.0,
+              double beta = 0.0);
+
+// y = H x for Hermitian H (n x n): uses H x = H^H x, one warp per entry.
+void zhemv_cols(cudaStream_t st, int n, const double2* H, const double2* x, double2* y);
+
+void hermitianize(cudaStream_t st, int k, double2* G, int ldg);
+void zero_strict_lower(cudaStream_t st, int k, double2* R, int ldr);
+void add_diag(cudaStream_t st, int k, double2* G, int ldg, const double* shift_dev);
+void column_norms(cudaStream_t st, int n, int k, const double2* Y, int ldy, double* out);
+void scale_columns_inv(cudaStream_t st, int n, int k, double2* Y, int ldy, const double* norms);
+void residual_norms(cudaStream_t st, int n, int k, const double2* HY, const double2* Y,
+                    const double* lam, double norm_h, double* out);
+void gather_columns(cudaStream_t st, int n, int k, const double2* src, int lds,
+                    const int* idx, double2* dst, int ldd);
+void gather_values(cudaStream_t st, int k, const double* src, const int* idx, double* dst);
+void copy_columns(cudaStream_t st, int n, int k, const double2* src, int lds, double2* dst,
+                  int ldd);
+// Shift for shifted CholQR from trace(G) (Fukaya et al., SISC 2020).
+void cholqr_shift(cudaStream_t st, int n, int k, const double2* G, int ldg, double* shift);
+int any_nonfinite(chfsi_ctx* ctx, size_t count, const double* v);
+
+// Lanczos helpers.
+void lanczos_start_vec(cudaStream_t st, int n, unsigned long long seed, double2* v);
+void vec_norm(cudaStream_t st, int n, const double2* v, double* out);
+void vec_scale_inv(cudaStream_t st, int n, const double2* w, const double* nrm, double2* v);
+void lanczos_alpha(cudaStream_t st, int j, const double2* h1, const double2* h2, double* alpha);
+void tridiag_bounds(cudaStream_t st, int m, const double* alpha, const double* beta,
+                    double* out4);
+
+// Loop control: locking, interval update, degrees, sorting (small_ops.cu).
+struct LoopCtl {
+  int n_new_locked;
+  int k_active;
+  int deg_max;
+  int nonfinite;
+  double alpha;
+  double gamma;
+  double max_resid_wanted;
+  double pad;
+};
+
+void lock_select(cudaStream_t st, int ka, const double* lam, const double* resid,
+                 int n_wanted_left, double tol, double gamma_in, LoopCtl* ctl,
+                 int* lock_idx, int* act_idx);
+void degrees_analytic(cudaStream_t st, int k, const double* ritz, const double* resid,
+                      const int* idx, double c, double e, double tol, int n_wanted,
+                      int deg_min, int deg_max, int deg_extra, int* deg_out);
+void sort_by_degree(cudaStream_t st, int k, const int* deg, const int* idx_or_null,
+                    int* perm, int* deg_sorted);
+void sort_by_value(cudaStream_t st, int k, const double* val, int* perm);
+void degree_cap_buffer(cudaStream_t st, int k, int n_wanted, int* deg);
+
+// Tensor-core split-precision filter (filter_tc.cu).
+int tc_filter_supported(chfsi_ctx* ctx);
+void tc_filter_prepare(chfsi_ctx* ctx, const double2* H, int n);
+void tc_filter_run(chfsi_ctx* ctx, const double2* H, int n, int k, const double2* Y0,
+                   const int* deg_host, double lam1, double c, double e, double2* Yout);
+void tc_filter_release(chfsi_ctx* ctx);
+
+// Degree MLP (mlp.cu).
+void mlp_create(chfsi_ctx* ctx);
+void mlp_destroy(chfsi_ctx* ctx);
+void mlp_set_params(chfsi_ctx* ctx, const float* host);
+void mlp_get_params(chfsi_ctx* ctx, float* host);
+void mlp_forward(chfsi_ctx* ctx, int B, const float* x, float* y);
+void mlp_train_step(chfsi_ctx* ctx, int B, const float* x, const float* target, float lr,
+                    float* grads, float* loss_dev);
+void mlp_degrees(chfsi_ctx* ctx, int k, const double* ritz, const double* resid,
+                 const int* idx, double c, double e, double gamma, int step, int* deg_out);

@@ -1,0 +1,528 @@
+// FP64 complex dense kernels of the ChFSI path: the NN product with the
+// fused three-term-recurrence epilogue (the FP64 Chebyshev filter step of
+// Alg. 2 line 8, and H*Q of the Rayleigh-Ritz step, Alg. 1 line 7), the
+// split-K conjugate-transpose product for the tall-skinny Gram and
+// projection matrices (Alg. 1 lines 6-7), the Hermitian mat-vec of the
+// Lanczos step (Alg. 1 line 3), and the column reductions for residuals.
+//
+// GB300 runs FP64 on a narrow pipe (about 1.1 TFLOP/s for the whole GPU),
+// so these kernels are bound by DFMA issue at any practical size: a 32 x 32
+// complex output tile per 256-thread CTA with a 2 x 2 register tile keeps
+// the pipe fed, and grids are sized to cover all 152 SMs several times.
+#include "common.cuh"
+
+namespace {
+
+constexpr int TB = 32;   // output tile edge (complex elements)
+constexpr int TK = 16;   // K chunk staged in shared memory
+
+__device__ __forceinline__ void cmac(double2& acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+
+// conj(a) * b accumulated.
+__device__ __forceinline__ void cmac_conj(double2& acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+
+__global__ void __launch_bounds__(256)
+zgemm_nn_kernel(int M, int N, int K, const double2* __restrict__ A, int lda,
+                const double2* __restrict__ B, int ldb, EpiNN ep) {
+  __shared__ double2 As[TK][TB + 1];
+  __shared__ double2 Bs[TK][TB + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int row0 = blockIdx.x * TB, col0 = blockIdx.y * TB;
+  double2 acc[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) acc[i][j] = make_double2(0.0, 0.0);
+
+  for (int k0 = 0; k0 < K; k0 += TK) {
+#pragma unroll
+    for (int e = threadIdx.x; e < TB * TK; e += 256) {
+      const int r = e & (TB - 1), kk = e >> 5;
+      const int gr = row0 + r, gk = k0 + kk;
+      As[kk][r] = (gr < M && gk < K) ? A[gr + (size_t)gk * lda] : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int e = threadIdx.x; e < TB * TK; e += 256) {
+      const int kk = e & (TK - 1), c = e >> 4;
+      const int gk = k0 + kk, gc = col0 + c;
+      Bs[kk][c] = (gk < K && gc < N) ? B[gk + (size_t)gc * ldb] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      const double2 a0 = As[kk][tx], a1 = As[kk][tx + 16];
+      const double2 b0 = Bs[kk][ty], b1 = Bs[kk][ty + 16];
+      cmac(acc[0][0], a0, b0);
+      cmac(acc[0][1], a0, b1);
+      cmac(acc[1][0], a1, b0);
+      cmac(acc[1][1], a1, b1);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int c = col0 + ty + 16 * j;
+    if (c >= N) continue;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int r = row0 + tx + 16 * i;
+      if (r >= M) continue;
+      double2 v = acc[i][j];
+      if (ep.shift != 0.0) {
+        const double2 s = ep.S[r + (size_t)c * ep.lds];
+        v.x = fma(-ep.shift, s.x, v.x);
+        v.y = fma(-ep.shift, s.y, v.y);
+      }
+      v.x *= ep.alpha;
+      v.y *= ep.alpha;
+      if (ep.beta != 0.0) {
+        const double2 p = ep.P[r + (size_t)c * ep.ldp];
+        v.x = fma(ep.beta, p.x, v.x);
+        v.y = fma(ep.beta, p.y, v.y);
+      }
+      ep.D[r + (size_t)c * ep.ldd] = v;
+      if (ep.F != nullptr && c < ep.fin_end) ep.F[r + (size_t)c * ep.ldf] = v;
+    }
+  }
+}
+
+// Partial[z] (K1 x K2) = A[rows of chunk z]^H B[rows of chunk z].
+__global__ void __launch_bounds__(256)
+zgemm_cn_part_kernel(int K1, int K2, int Nr, int chunk, const double2* __restrict__ A,
+                     int lda, const double2* __restrict__ B, int ldb,
+                     double2* __restrict__ part) {
+  __shared__ double2 As[TK][TB + 1];
+  __shared__ double2 Bs[TK][TB + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i0 = blockIdx.x * TB, j0 = blockIdx.y * TB;
+  const int rbeg = blockIdx.z * chunk;
+  const int rend = min(Nr, rbeg + chunk);
+  double2 acc[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) acc[i][j] = make_double2(0.0, 0.0);
+  for (int r0 = rbeg; r0 < rend; r0 += TK) {
+#pragma unroll
+    for (int e = threadIdx.x; e < TB * TK; e += 256) {
+      const int rr = e & (TK - 1), c = e >> 4;
+      const int gr = r0 + rr;
+      As[rr][c] = (gr < rend && i0 + c < K1) ? A[gr + (size_t)(i0 + c) * lda]
+                                             : make_double2(0.0, 0.0);
+      Bs[rr][c] = (gr < rend && j0 + c < K2) ? B[gr + (size_t)(j0 + c) * ldb]
+                                             : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rr = 0; rr < TK; ++rr) {
+      const double2 a0 = As[rr][tx], a1 = As[rr][tx + 16];
+      const double2 b0 = Bs[rr][ty], b1 = Bs[rr][ty + 16];
+      cmac_conj(acc[0][0], a0, b0);
+      cmac_conj(acc[0][1], a0, b1);
+      cmac_conj(acc[1][0], a1, b0);
+      cmac_conj(acc[1][1], a1, b1);
+    }
+    __syncthreads();
+  }
+  double2* out = part + (size_t)blockIdx.z * K1 * K2;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int c = j0 + ty + 16 * j;
+    if (c >= K2) continue;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int r = i0 + tx + 16 * i;
+      if (r < K1) out[r + (size_t)c * K1] = acc[i][j];
+    }
+  }
+}
+
+__global__ void zgemm_cn_reduce_kernel(int K1, int K2, int splits, const double2* part,
+                                       double2* C, int ldc, double alpha, double beta) {
+  const size_t total = (size_t)K1 * K2;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int z = 0; z < splits; ++z) {
+      const double2 p = part[(size_t)z * total + t];
+      s.x += p.x;
+      s.y += p.y;
+    }
+    const int i = (int)(t % K1), j = (int)(t / K1);
+    double2* c = C + i + (size_t)j * ldc;
+    double2 v = make_double2(alpha * s.x, alpha * s.y);
+    if (beta != 0.0) {
+      v.x = fma(beta, c->x, v.x);
+      v.y = fma(beta, c->y, v.y);
+    }
+    *c = v;
+  }
+}
+
+// y[r] = sum_j conj(H[j, r]) x[j]  (= (H x)[r] for Hermitian H).
+__global__ void zhemv_cols_kernel(int n, const double2* __restrict__ H,
+                                  const double2* __restrict__ x, double2* __restrict__ y) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double2* col = H + (size_t)warp * n;
+  double2 s = make_double2(0.0, 0.0);
+  for (int j = lane; j < n; j += 32) cmac_conj(s, col[j], x[j]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+    s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+  }
+  if (lane == 0) y[warp] = s;
+}
+
+template <int NT>
+__device__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (l < NT / 32) ? sh[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
+  __syncthreads();
+  return v;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(256)
+column_norms_kernel(int n, const double2* __restrict__ Y, int ldy, double* out) {
+  __shared__ double sh[8];
+  const double2* y = Y + (size_t)blockIdx.x * ldy;
+  double s = 0.0;
+  for (int r = threadIdx.x; r < n; r += 256) s += y[r].x * y[r].x + y[r].y * y[r].y;
+  s = block_sum<256>(s, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = sqrt(s);
+}
+
+__global__ void scale_columns_inv_kernel(int n, int k, double2* Y, int ldy,
+                                         const double* norms) {
+  const int c = blockIdx.y;
+  const double inv = 1.0 / norms[c];
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    double2 v = Y[r + (size_t)c * ldy];
+    v.x *= inv;
+    v.y *= inv;
+    Y[r + (size_t)c * ldy] = v;
+  }
+}
+
+__global__ void __launch_bounds__(256)
+residual_norms_kernel(int n, const double2* __restrict__ HY, const double2* __restrict__ Y,
+                      const double* lam, double inv_norm, double* out) {
+  __shared__ double sh[8];
+  const size_t off = (size_t)blockIdx.x * n;
+  const double l = lam[blockIdx.x];
+  double s = 0.0;
+  for (int r = threadIdx.x; r < n; r += 256) {
+    const double2 h = HY[off + r], y = Y[off + r];
+    const double dx = h.x - l * y.x, dy = h.y - l * y.y;
+    s += dx * dx + dy * dy;
+  }
+  s = block_sum<256>(s, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = sqrt(s) * inv_norm;
+}
+
+__global__ void hermitianize_kernel(int k, double2* G, int ldg) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i > j || j >= k) return;
+  double2 a = G[i + (size_t)j * ldg], b = G[j + (size_t)i * ldg];
+  if (i == j) {
+    G[i + (size_t)j * ldg] = make_double2(a.x, 0.0);
+    return;
+  }
+  const double2 v = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+  G[i + (size_t)j * ldg] = v;
+  G[j + (size_t)i * ldg] = make_double2(v.x, -v.y);
+}
+
+__global__ void zero_strict_lower_kernel(int k, double2* R, int ldr) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i < k && i > j) R[i + (size_t)j * ldr] = make_double2(0.0, 0.0);
+}
+
+__global__ void add_diag_kernel(int k, double2* G, int ldg, const double* shift) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < k) G[i + (size_t)i * ldg].x += *shift;
+}
+
+__global__ void gather_columns_kernel(int n, const double2* __restrict__ src, int lds,
+                                      const int* __restrict__ idx, double2* __restrict__ dst,
+                                      int ldd) {
+  const int c = blockIdx.y;
+  const int sc = idx ? idx[c] : c;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x)
+    dst[r + (size_t)c * ldd] = src[r + (size_t)sc * lds];
+}
+
+__global__ void gather_values_kernel(int k, const double* src, const int* idx, double* dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < k) dst[i] = src[idx[i]];
+}
+
+// Shifted CholQR shift s = 11 (n k + k (k + 1)) u ||Y||_2^2 with the
+// bound ||Y||_2^2 <= trace(G) (Fukaya, Kannan, Nakatsukasa, Yamamoto,
+// Yanagisawa, SIAM J. Sci. Comput. 42 (2020), Sec. 3).
+__global__ void cholqr_shift_kernel(int n, int k, const double2* G, int ldg, double* shift) {
+  __shared__ double sh[8];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < k; i += 256) s += G[i + (size_t)i * ldg].x;
+  s = block_sum<256>(s, sh);
+  if (threadIdx.x == 0) {
+    const double u = 1.1102230246251565e-16;
+    *shift = 11.0 * ((double)n * k + (double)k * (k + 1)) * u * s;
+  }
+}
+
+__global__ void nonfinite_kernel(size_t count, const double* v, int* flag) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x)
+    if (!isfinite(v[i])) *flag = 1;
+}
+
+// ---- Lanczos pieces ------------------------------------------------------
+__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed,
+                                                            unsigned long long t) {
+  unsigned long long z = seed + (t + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void lanczos_start_kernel(int n, unsigned long long seed, double2* v) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double sc = 1.1102230246251565e-16;  // 2^-53
+  const unsigned long long a = splitmix64_at(seed, 2ull * j) >> 11;
+  const unsigned long long b = splitmix64_at(seed, 2ull * j + 1ull) >> 11;
+  v[j] = make_double2((double)a * sc * 2.0 - 1.0, (double)b * sc * 2.0 - 1.0);
+}
+
+__global__ void __launch_bounds__(1024) vec_norm_kernel(int n, const double2* v, double* out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int r = threadIdx.x; r < n; r += 1024) s += v[r].x * v[r].x + v[r].y * v[r].y;
+  s = block_sum<1024>(s, sh);
+  if (threadIdx.x == 0) *out = sqrt(s);
+}
+
+__global__ void vec_scale_inv_kernel(int n, const double2* w, const double* nrm, double2* v) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const double inv = 1.0 / *nrm;
+  v[r] = make_double2(w[r].x * inv, w[r].y * inv);
+}
+
+__global__ void lanczos_alpha_kernel(int j, const double2* h1, const double2* h2,
+                                     double* alpha) {
+  alpha[j] = h1[j].x + h2[j].x;
+}
+
+// Number of eigenvalues of the symmetric tridiagonal (a, b) below x
+// (Sturm sequence count with the LDL^T pivots).
+__device__ int sturm_count(int m, const double* a, const double* b, double x) {
+  int cnt = 0;
+  double d = 1.0;
+  for (int i = 0; i < m; ++i) {
+    const double bb = (i > 0) ? b[i - 1] * b[i - 1] : 0.0;
+    d = (a[i] - x) - ((i > 0) ? bb / d : 0.0);
+    if (d == 0.0) d = -1e-300;
+    if (d < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// Extreme eigenvalues of the Lanczos tridiagonal by bisection on Sturm
+// counts; out4 = {theta_max + beta_m, theta_min, theta_max, max|theta|},
+// beta_m the norm of the last residual vector.
+__global__ void tridiag_bounds_kernel(int m_in, const double* a, const double* b, double* out) {
+  if (threadIdx.x != 0) return;
+  // Steps after an (almost) invariant Krylov space are not used: the
+  // recurrence stops at the first beta_j <= 1e-14 max(|alpha_j|, 1).
+  int m = m_in;
+  for (int j = 0; j < m_in; ++j)
+    if (!(b[j] > 1e-14 * fmax(fabs(a[j]), 1.0))) { m = j + 1; break; }
+  double lo = a[0], hi = a[0];
+  for (int i = 0; i < m; ++i) {
+    const double r = ((i > 0) ? fabs(b[i - 1]) : 0.0) + ((i < m - 1) ? fabs(b[i]) : 0.0);
+    lo = fmin(lo, a[i] - r);
+    hi = fmax(hi, a[i] + r);
+  }
+  double th[2];
+  for (int which = 0; which < 2; ++which) {
+    const int target = which == 0 ? 1 : m;  // count below x >= target
+    double l = lo - 1e-12 * fabs(lo) - 1e-300, h = hi + 1e-12 * fabs(hi) + 1e-300;
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (l + h);
+      if (mid <= l || mid >= h) break;
+      if (sturm_count(m, a, b, mid) >= target) h = mid; else l = mid;
+    }
+    th[which] = 0.5 * (l + h);
+  }
+  out[1] = th[0];
+  out[2] = th[1];
+  out[0] = th[1] + b[m - 1];
+  out[3] = fmax(fabs(th[0]), fabs(th[1]));
+}
+
+int grid_for(size_t work, int per_block, int cap = 4096) {
+  size_t g = (work + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > (size_t)cap) g = cap;
+  return (int)g;
+}
+
+}  // namespace
+
+// ======================================================== host wrappers ===
+void zgemm_nn(cudaStream_t st, int M, int N, int K, const double2* A, int lda,
+              const double2* B, int ldb, const EpiNN& ep) {
+  if (M <= 0 || N <= 0) return;
+  dim3 grid((M + TB - 1) / TB, (N + TB - 1) / TB);
+  zgemm_nn_kernel<<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, ep);
+  chfsi_check_launch("zgemm_nn");
+}
+
+void zgemm_cn(chfsi_ctx* ctx, int K1, int K2, int Nr, const double2* A, int lda,
+              const double2* B, int ldb, double2* C, int ldc, double alpha, double beta) {
+  if (K1 <= 0 || K2 <= 0) return;
+  const int tiles = ((K1 + TB - 1) / TB) * ((K2 + TB - 1) / TB);
+  int splits = (4 * ctx->sm_count + tiles - 1) / tiles;
+  const int max_splits = (Nr + 63) / 64;
+  if (splits > max_splits) splits = max_splits;
+  if (splits < 1) splits = 1;
+  int chunk = (Nr + splits - 1) / splits;
+  chunk = (chunk + TK - 1) / TK * TK;
+  splits = (Nr + chunk - 1) / chunk;
+  if (splits < 1) splits = 1;
+  double2* part = (double2*)ws_get(ctx, "cn_part", sizeof(double2) * (size_t)splits * K1 * K2);
+  dim3 grid((K1 + TB - 1) / TB, (K2 + TB - 1) / TB, splits);
+  zgemm_cn_part_kernel<<<grid, 256, 0, ctx->stream>>>(K1, K2, Nr, chunk, A, lda, B, ldb, part);
+  chfsi_check_launch("zgemm_cn_part");
+  zgemm_cn_reduce_kernel<<<grid_for((size_t)K1 * K2, 256, 2048), 256, 0, ctx->stream>>>(
+      K1, K2, splits, part, C, ldc, alpha, beta);
+  chfsi_check_launch("zgemm_cn_reduce");
+}
+
+void zhemv_cols(cudaStream_t st, int n, const double2* H, const double2* x, double2* y) {
+  zhemv_cols_kernel<<<(n + 7) / 8, 256, 0, st>>>(n, H, x, y);
+  chfsi_check_launch("zhemv_cols");
+}
+
+void hermitianize(cudaStream_t st, int k, double2* G, int ldg) {
+  if (k <= 0) return;
+  hermitianize_kernel<<<dim3((k + 127) / 128, k), 128, 0, st>>>(k, G, ldg);
+  chfsi_check_launch("hermitianize");
+}
+
+void zero_strict_lower(cudaStream_t st, int k, double2* R, int ldr) {
+  if (k <= 0) return;
+  zero_strict_lower_kernel<<<dim3((k + 127) / 128, k), 128, 0, st>>>(k, R, ldr);
+  chfsi_check_launch("zero_strict_lower");
+}
+
+void add_diag(cudaStream_t st, int k, double2* G, int ldg, const double* shift_dev) {
+  add_diag_kernel<<<(k + 255) / 256, 256, 0, st>>>(k, G, ldg, shift_dev);
+  chfsi_check_launch("add_diag");
+}
+
+void column_norms(cudaStream_t st, int n, int k, const double2* Y, int ldy, double* out) {
+  if (k <= 0) return;
+  column_norms_kernel<<<k, 256, 0, st>>>(n, Y, ldy, out);
+  chfsi_check_launch("column_norms");
+}
+
+void scale_columns_inv(cudaStream_t st, int n, int k, double2* Y, int ldy,
+                       const double* norms) {
+  if (k <= 0) return;
+  scale_columns_inv_kernel<<<dim3(grid_for(n, 256, 64), k), 256, 0, st>>>(n, k, Y, ldy, norms);
+  chfsi_check_launch("scale_columns_inv");
+}
+
+void residual_norms(cudaStream_t st, int n, int k, const double2* HY, const double2* Y,
+                    const double* lam, double norm_h, double* out) {
+  if (k <= 0) return;
+  residual_norms_kernel<<<k, 256, 0, st>>>(n, HY, Y, lam, 1.0 / norm_h, out);
+  chfsi_check_launch("residual_norms");
+}
+
+void gather_columns(cudaStream_t st, int n, int k, const double2* src, int lds, const int* idx,
+                    double2* dst, int ldd) {
+  if (k <= 0) return;
+  gather_columns_kernel<<<dim3(grid_for(n, 256, 64), k), 256, 0, st>>>(n, src, lds, idx, dst,
+                                                                        ldd);
+  chfsi_check_launch("gather_columns");
+}
+
+void copy_columns(cudaStream_t st, int n, int k, const double2* src, int lds, double2* dst,
+                  int ldd) {
+  gather_columns(st, n, k, src, lds, nullptr, dst, ldd);
+}
+
+void gather_values(cudaStream_t st, int k, const double* src, const int* idx, double* dst) {
+  if (k <= 0) return;
+  gather_values_kernel<<<(k + 255) / 256, 256, 0, st>>>(k, src, idx, dst);
+  chfsi_check_launch("gather_values");
+}
+
+void cholqr_shift(cudaStream_t st, int n, int k, const double2* G, int ldg, double* shift) {
+  cholqr_shift_kernel<<<1, 256, 0, st>>>(n, k, G, ldg, shift);
+  chfsi_check_launch("cholqr_shift");
+}
+
+int any_nonfinite(chfsi_ctx* ctx, size_t count, const double* v) {
+  int* flag = (int*)ws_get(ctx, "nf_flag", sizeof(int));
+  CHFSI_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), ctx->stream));
+  nonfinite_kernel<<<grid_for(count, 256, 1024), 256, 0, ctx->stream>>>(count, v, flag);
+  chfsi_check_launch("nonfinite");
+  int* h = (int*)pinned_get(ctx, 64);
+  CHFSI_CUDA_TRY(cudaMemcpyAsync(h, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CHFSI_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return *h;
+}
+
+void lanczos_start_vec(cudaStream_t st, int n, unsigned long long seed, double2* v) {
+  lanczos_start_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, seed, v);
+  chfsi_check_launch("lanczos_start");
+}
+
+void vec_norm(cudaStream_t st, int n, const double2* v, double* out) {
+  vec_norm_kernel<<<1, 1024, 0, st>>>(n, v, out);
+  chfsi_check_launch("vec_norm");
+}
+
+void vec_scale_inv(cudaStream_t st, int n, const double2* w, const double* nrm, double2* v) {
+  vec_scale_inv_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, w, nrm, v);
+  chfsi_check_launch("vec_scale_inv");
+}
+
+void lanczos_alpha(cudaStream_t st, int j, const double2* h1, const double2* h2,
+                   double* alpha) {
+  lanczos_alpha_kernel<<<1, 1, 0, st>>>(j, h1, h2, alpha);
+  chfsi_check_launch("lanczos_alpha");
+}
+
+void tridiag_bounds(cudaStream_t st, int m, const double* alpha, const double* beta,
+                    double* out4) {
+  tridiag_bounds_kernel<<<1, 32, 0, st>>>(m, alpha, beta, out4);
+  chfsi_check_launch("tridiag_bounds");
+}

@@ -1,0 +1,48 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol
+that include/chfsi.h declares (no GPU needed)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1404_4161_gb300.build import build
+    return build()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "chfsi.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(chfsi_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for need in ["chfsi_init", "chfsi_solve", "chfsi_solve_sequence", "chfsi_free",
+                 "chfsi_filter", "chfsi_lanczos", "chfsi_orthonormalize",
+                 "chfsi_rayleigh_ritz", "chfsi_residuals", "chfsi_degrees"]:
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(l.split()[-1] for l in out.splitlines() if l.strip())
+    missing = [f for f in declared_functions() if f not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_binding_matches(libpath):
+    from paper_1404_4161_gb300 import _lib
+    h = _lib.lib()
+    for name in declared_functions():
+        assert hasattr(h, name)
+    assert set(_lib.exported_names()) == set(declared_functions())
+    o = _lib.default_opts()
+    assert (o.deg_max, o.deg_extra, o.lanczos_steps) == (36, 1, 20)
+    assert _lib.lib().chfsi_strerror(_lib.ENOCONV) == b"not converged within max_loops"
