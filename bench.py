@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["mixed", "fp64"], default="fp64")
+    ap.add_argument("--precision", choices=["tc", "mixed", "fp64"], default="tc")
     ap.add_argument("--n", type=int, default=None, help="override n (smaller test runs)")
     ap.add_argument("--length", type=int, default=None)
     ap.add_argument("--fp64-compare", type=int, default=0,
@@ -213,7 +213,7 @@ def main():
     X0c = colmajor(torch.from_numpy(X0).to(dev))
     torch.cuda.synchronize()
 
-    prec = L.PREC_MIXED if args.precision == "mixed" else L.PREC_FP64
+    prec = {"tc": L.PREC_TC, "mixed": L.PREC_MIXED, "fp64": L.PREC_FP64}[args.precision]
     s = Chfsi(precision=prec)
     stream = torch.cuda.current_stream()
 
@@ -322,7 +322,7 @@ def main():
             "metric": METRIC, "value": sec_per_problem, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if prec == L.PREC_FP64 else "bf16x3+f64",
+            "dtype": "f64" if prec == L.PREC_FP64 else "bf16x3 (filter) + f64",
             "data": "synthetic",
             "config": {"workload": f"correlated sequence of {length} complex128 Hermitian "
                                    f"problems, n={n}, nev={nev}, nex={nex}, eps=1e-3, "

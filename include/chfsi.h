@@ -45,6 +45,10 @@ extern "C" {
 #define CHFSI_PREC_MIXED 1  /* split-precision tensor-core filter while the  */
                             /* largest wanted residual > switch_tol, then    */
                             /* FP64 filter sweeps to tol                     */
+#define CHFSI_PREC_TC 2     /* split-precision tensor-core filter in every   */
+                            /* loop; from the second loop on it filters the  */
+                            /* residual block (chfsi_filter_refine), so its  */
+                            /* error scales with the residual: no FP64 sweep */
 
 /* Split format of the tensor-core filter (CHFSI_PREC_MIXED). */
 #define CHFSI_SPLIT_BF16X3 0 /* x = hi + lo in bf16; hi*hi + hi*lo + lo*hi   */
@@ -57,7 +61,7 @@ extern "C" {
 typedef struct chfsi_ctx chfsi_ctx;
 
 typedef struct chfsi_opts {
-  int precision;       /* CHFSI_PREC_*                        (FP64)       */
+  int precision;       /* CHFSI_PREC_FP64 / _MIXED / _TC      (FP64)       */
   int split;           /* CHFSI_SPLIT_*                       (BF16X3)     */
   int degree_model;    /* CHFSI_DEG_*                         (ANALYTIC)   */
   int deg_cold;        /* first-loop degree, random start     (20)         */
@@ -121,8 +125,8 @@ const char* chfsi_last_error(const chfsi_ctx* ctx);
  *         and within the rest, matching X's columns.
  *  warm_host  NULL for a random start, else two doubles {lam_1, lam_k} of
  *         the previous problem (Alg. 1 Require line): gamma and alpha.
- *  Requires 1 <= nev, 1 <= nex, nev + nex <= n.  On ENOCONV / EBREAKDOWN X
- *  holds the last orthonormal iterate. */
+ *  Requires 1 <= nev, 1 <= nex, nev + nex <= n.  On ENOCONV X holds the
+ *  last block of Ritz vectors; on any other error X is left unchanged. */
 int chfsi_solve(chfsi_ctx* ctx, const double* H, int n, int nev, int nex,
                 double* X, double tol, double* evals,
                 const double* warm_host, chfsi_stats* stats_host);
@@ -163,6 +167,21 @@ int chfsi_lanczos(chfsi_ctx* ctx, const double* H, int n, int steps,
 int chfsi_filter(chfsi_ctx* ctx, const double* H, int n, int k, const double* Y0,
                  const int* degrees_host, double lam1, double c, double e,
                  double* Y, int precision);
+
+/* Alg. 2 in refinement form (not in the paper): for Ritz pairs (Y, ritz)
+ * of H and R = H Y - Y diag(ritz), returns Y_m = p_m(H) Y exactly as
+ * chfsi_filter would, computed as Y psi_m(ritz) + D_m: psi_m is the
+ * filter's scalar recurrence on each Ritz value (FP64) and D_m the same
+ * three-term recurrence driven by R (D_0 = 0, D_1 = a_0 R, D_{i+1} =
+ * a_i (H D_i - c D_i) + b_i D_{i-1} + a_i psi_i(ritz) R), computed with
+ * the split-precision tensor-core product.  Its error is the split
+ * precision times ||R|| rather than times ||Y||.
+ *  Y, R   complex n x k (device), columns in ascending-degree order.
+ *  ritz   k doubles (device); degrees_host as for chfsi_filter.
+ *  Yout   complex n x k (device), may not alias Y or R. */
+int chfsi_filter_refine(chfsi_ctx* ctx, const double* H, int n, int k, const double* Y,
+                        const double* R, const double* ritz, const int* degrees_host,
+                        double lam1, double c, double e, double* Yout);
 
 /* Alg. 1 line 6: orthonormalise the k columns of Y (complex n x k, in
  * place) against the nl orthonormal columns of L (complex n x nl; may be

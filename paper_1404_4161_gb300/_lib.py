@@ -12,7 +12,7 @@ import os
 from .build import LIB
 
 OK, EINVAL, ENOMEM, ENOCONV, EBREAKDOWN, ENAN, ETIMEOUT, ECUDA, ENOTSUP = range(9)
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_TC = 0, 1, 2
 SPLIT_BF16X3, SPLIT_FP16X3 = 0, 1
 DEG_ANALYTIC, DEG_MLP = 0, 1
 MLP_NPARAM = 64 * 5 + 64 + 64 * 64 + 64 + 64 + 1
@@ -64,6 +64,8 @@ _SIGS = {
     "chfsi_lanczos": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_ulonglong, _P]),
     "chfsi_filter": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, C.c_double, C.c_double,
                                C.c_double, _P, C.c_int]),
+    "chfsi_filter_refine": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, _P, _P, C.c_double,
+                                      C.c_double, C.c_double, _P]),
     "chfsi_orthonormalize": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_int, _P]),
     "chfsi_rayleigh_ritz": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, _P, _P]),
     "chfsi_residuals": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P, C.c_double, _P]),

@@ -67,7 +67,8 @@ namespace {
 int run_guarded(chfsi_ctx* ctx, const std::function<void()>& body);
 
 void validate_opts(const chfsi_opts& o) {
-  CHFSI_REQUIRE(o.precision == CHFSI_PREC_FP64 || o.precision == CHFSI_PREC_MIXED,
+  CHFSI_REQUIRE(o.precision == CHFSI_PREC_FP64 || o.precision == CHFSI_PREC_MIXED ||
+                    o.precision == CHFSI_PREC_TC,
                 "opts.precision");
   CHFSI_REQUIRE(o.split == CHFSI_SPLIT_BF16X3 || o.split == CHFSI_SPLIT_FP16X3, "opts.split");
   CHFSI_REQUIRE(o.degree_model == CHFSI_DEG_ANALYTIC || o.degree_model == CHFSI_DEG_MLP,
@@ -342,7 +343,8 @@ int solve_one(chfsi_ctx* ctx, const double2* H, int n, int nev, int nex, double2
   CHFSI_REQUIRE(nev >= 1 && nex >= 1 && k <= n, "need 1 <= nev, 1 <= nex, nev + nex <= n");
   CHFSI_REQUIRE(tol > 0.0, "tol must be > 0");
   const bool mixed = o.precision == CHFSI_PREC_MIXED;
-  if (mixed && !tc_filter_supported(ctx))
+  const bool tc_all = o.precision == CHFSI_PREC_TC;
+  if ((mixed || tc_all) && !tc_filter_supported(ctx))
     throw ChfsiError{CHFSI_ENOTSUP, "split-precision filter needs an sm_103 device"};
 
   chfsi_stats S;
@@ -361,6 +363,8 @@ int solve_one(chfsi_ctx* ctx, const double2* H, int n, int nev, int nex, double2
   double* res = (double*)ws_get(ctx, "s_res", sizeof(double) * k);
   double* lamL = (double*)ws_get(ctx, "s_lamL", sizeof(double) * nev);
   double* resL = (double*)ws_get(ctx, "s_resL", sizeof(double) * nev);
+  double2* Rblk = tc_all ? (double2*)ws_get(ctx, "s_Rblk", blk) : nullptr;
+  double* lam_act = (double*)ws_get(ctx, "s_lamact", sizeof(double) * k);
   int* iws = (int*)ws_get(ctx, "s_int", sizeof(int) * 5 * (size_t)k);
   int* lock_idx = iws;
   int* act_idx = iws + k;
@@ -418,7 +422,15 @@ int solve_one(chfsi_ctx* ctx, const double2* H, int n, int nev, int nex, double2
     for (int j = 0; j < ka; ++j) sdeg += degs[j];
     tm.mark(2);
     const long long fl0 = chfsi_launch_counter();
-    if (lowp_on) {
+    if (tc_all) {
+      if (loops == 1)
+        tc_filter_run(ctx, H, n, ka, Xact, degs.data(), gamma, c, e, Yf);
+      else
+        tc_filter_run_defect(ctx, H, n, ka, Xact, Rblk, lam_act, degs.data(), deg_sorted, gamma,
+                             c, e, Yf);
+      S.loops_lowp++;
+      S.col_degrees_lowp += sdeg;
+    } else if (lowp_on) {
       tc_filter_run(ctx, H, n, ka, Xact, degs.data(), gamma, c, e, Yf);
       S.loops_lowp++;
       S.col_degrees_lowp += sdeg;
@@ -462,6 +474,7 @@ int solve_one(chfsi_ctx* ctx, const double2* H, int n, int nev, int nex, double2
       }
       sort_by_degree(st, ka, deg, act_idx, perm, deg_sorted);
       gather_columns(st, n, ka, Yrr, n, perm, Xact, n);
+      if (tc_all) residual_block(st, n, ka, HY, Yrr, lam, perm, Rblk, lam_act);
       CHFSI_CUDA_TRY(cudaMemcpyAsync(deg_h, deg_sorted, sizeof(int) * ka,
                                      cudaMemcpyDeviceToHost, st));
       tm.mark(7);
@@ -571,7 +584,7 @@ int chfsi_init(chfsi_ctx** out, const chfsi_opts* opts, void* stream) {
     CHFSI_SOLVER_TRY(cusolverDnCreate(&ctx->solver));
     CHFSI_SOLVER_TRY(cusolverDnSetStream(ctx->solver, ctx->stream));
     for (auto& e : ctx->ev) CHFSI_CUDA_TRY(cudaEventCreate(&e));
-    if (ctx->opts.precision == CHFSI_PREC_MIXED && !tc_filter_supported(ctx))
+    if (ctx->opts.precision != CHFSI_PREC_FP64 && !tc_filter_supported(ctx))
       throw ChfsiError{CHFSI_ENOTSUP, "split-precision filter needs an sm_103 device"};
     mlp_create(ctx);
   });
@@ -587,7 +600,7 @@ int chfsi_set_opts(chfsi_ctx* ctx, const chfsi_opts* opts) {
   if (!ctx || !opts) return CHFSI_EINVAL;
   return run_guarded(ctx, [&] {
     validate_opts(*opts);
-    if (opts->precision == CHFSI_PREC_MIXED && !tc_filter_supported(ctx))
+    if (opts->precision != CHFSI_PREC_FP64 && !tc_filter_supported(ctx))
       throw ChfsiError{CHFSI_ENOTSUP, "split-precision filter needs an sm_103 device"};
     ctx->opts = *opts;
   });
@@ -719,7 +732,7 @@ int chfsi_filter(chfsi_ctx* ctx, const double* H, int n, int k, const double* Y0
       CHFSI_REQUIRE(j == 0 || degrees_host[j] >= degrees_host[j - 1],
                     "degrees must be ascending");
     }
-    if (precision == CHFSI_PREC_MIXED) {
+    if (precision == CHFSI_PREC_MIXED || precision == CHFSI_PREC_TC) {
       if (!tc_filter_supported(ctx))
         throw ChfsiError{CHFSI_ENOTSUP, "split-precision filter needs an sm_103 device"};
       tc_filter_run(ctx, C2(H), n, k, C2(Y0), degrees_host, lam1, c, e, C2(Y));
@@ -727,6 +740,31 @@ int chfsi_filter(chfsi_ctx* ctx, const double* H, int n, int k, const double* Y0
       CHFSI_REQUIRE(precision == CHFSI_PREC_FP64, "bad precision");
       filter_f64(ctx, C2(H), n, k, C2(Y0), degrees_host, lam1, c, e, C2(Y));
     }
+  });
+}
+
+int chfsi_filter_refine(chfsi_ctx* ctx, const double* H, int n, int k, const double* Y,
+                        const double* R, const double* ritz, const int* degrees_host,
+                        double lam1, double c, double e, double* Yout) {
+  if (!ctx) return CHFSI_EINVAL;
+  return run_guarded(ctx, [&] {
+    CHFSI_REQUIRE(n >= 1 && k >= 0 && k <= n, "bad filter sizes");
+    if (k == 0) return;
+    CHFSI_REQUIRE(H && Y && R && ritz && Yout && degrees_host && Yout != Y && Yout != R,
+                  "bad filter buffers");
+    CHFSI_REQUIRE(e > 0.0 && lam1 != c, "bad filter interval");
+    for (int j = 0; j < k; ++j) {
+      CHFSI_REQUIRE(degrees_host[j] >= 1, "degrees must be >= 1");
+      CHFSI_REQUIRE(j == 0 || degrees_host[j] >= degrees_host[j - 1],
+                    "degrees must be ascending");
+    }
+    if (!tc_filter_supported(ctx))
+      throw ChfsiError{CHFSI_ENOTSUP, "split-precision filter needs an sm_103 device"};
+    int* dd = (int*)ws_get(ctx, "api_deg", sizeof(int) * k);
+    CHFSI_CUDA_TRY(cudaMemcpyAsync(dd, degrees_host, sizeof(int) * k, cudaMemcpyHostToDevice,
+                                   ctx->stream));
+    tc_filter_run_defect(ctx, C2(H), n, k, C2(Y), C2(R), ritz, degrees_host, dd, lam1, c, e,
+                         C2(Yout));
   });
 }
 

@@ -173,7 +173,13 @@ int tc_filter_supported(chfsi_ctx* ctx);
 void tc_filter_prepare(chfsi_ctx* ctx, const double2* H, int n);
 void tc_filter_run(chfsi_ctx* ctx, const double2* H, int n, int k, const double2* Y0,
                    const int* deg_host, double lam1, double c, double e, double2* Yout);
+void tc_filter_run_defect(chfsi_ctx* ctx, const double2* H, int n, int k, const double2* Y,
+                          const double2* Rres, const double* lam, const int* deg_host,
+                          const int* deg_dev, double lam1, double c, double e, double2* Yout);
 void tc_filter_release(chfsi_ctx* ctx);
+// R[:, j] = HY[:, perm[j]] - lam[perm[j]] Y[:, perm[j]], lam_out[j] = lam[perm[j]].
+void residual_block(cudaStream_t st, int n, int k, const double2* HY, const double2* Y,
+                    const double* lam, const int* perm, double2* R, double* lam_out);
 
 // Degree MLP (mlp.cu).
 void mlp_create(chfsi_ctx* ctx);

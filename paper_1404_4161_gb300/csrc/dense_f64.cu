@@ -384,6 +384,21 @@ __global__ void tridiag_bounds_kernel(int m_in, const double* a, const double* b
   out[3] = fmax(fabs(th[0]), fabs(th[1]));
 }
 
+__global__ void residual_block_kernel(int n, const double2* __restrict__ HY,
+                                      const double2* __restrict__ Y, const double* lam,
+                                      const int* __restrict__ perm, double2* __restrict__ R,
+                                      double* lam_out) {
+  const int j = blockIdx.y;
+  const int sj = perm[j];
+  const double l = lam[sj];
+  if (blockIdx.x == 0 && threadIdx.x == 0) lam_out[j] = l;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const size_t es = (size_t)r + (size_t)sj * n;
+    const double2 h = HY[es], y = Y[es];
+    R[(size_t)r + (size_t)j * n] = make_double2(h.x - l * y.x, h.y - l * y.y);
+  }
+}
+
 int grid_for(size_t work, int per_block, int cap = 4096) {
   size_t g = (work + per_block - 1) / per_block;
   if (g < 1) g = 1;
@@ -525,4 +540,12 @@ void tridiag_bounds(cudaStream_t st, int m, const double* alpha, const double* b
                     double* out4) {
   tridiag_bounds_kernel<<<1, 32, 0, st>>>(m, alpha, beta, out4);
   chfsi_check_launch("tridiag_bounds");
+}
+
+void residual_block(cudaStream_t st, int n, int k, const double2* HY, const double2* Y,
+                    const double* lam, const int* perm, double2* R, double* lam_out) {
+  if (k <= 0) return;
+  residual_block_kernel<<<dim3(grid_for(n, 256, 64), k), 256, 0, st>>>(n, HY, Y, lam, perm, R,
+                                                                        lam_out);
+  chfsi_check_launch("residual_block");
 }

@@ -1,16 +1,698 @@
-// Split-precision tensor-core Chebyshev filter (placeholder until the
-// tcgen05 kernel lands): reports "not supported" so the solver refuses the
-// mixed path rather than falling back.
+// Split-precision Chebyshev filter on the GB300 tensor cores (tcgen05 +
+// TMEM + TMA), sm_103a.
+//
+// Each step of Alg. 2 (line 8) computes Y_{i+1} = a_i (H Y_i - c Y_i) +
+// b_i Y_{i-1} on the active (still unfinished) suffix of the degree-sorted
+// block.  The complex product is one real GEMM
+//
+//     [Hr | Hi] (n x 2n)  *  B (2n x 2k)  ->  [.. Zr_j, Zi_j ..] (n x 2k)
+//
+// with B's columns interleaved per complex column j: column 2j holds
+// (Yr_j ; -Yi_j) and column 2j+1 holds (Yi_j ; Yr_j), so the real and
+// imaginary parts of each output element sit in adjacent accumulator
+// columns.  A = [Hr | Hi] is built once per problem (row r of A is the
+// conjugate of column r of the Hermitian H, read contiguously).
+//
+// Split format BF16x3: x = hi + lo with hi = bf16(x), lo = bf16(x - hi);
+// the product uses hi*hi + hi*lo + lo*hi, all accumulated in one FP32 TMEM
+// accumulator (the lo*lo term is below the kept precision).
+//
+// Kernel layout (one 128 x N output tile per CTA, 256 threads):
+//   warp 0 lane 0: TMA producer (A_hi, A_lo, B_hi, B_lo tiles per K block)
+//   warp 1 lane 0: tcgen05.mma issuer (3 products x 4 K-steps per block)
+//   warp 2:        TMEM allocation / release
+//   warps 4-7:     epilogue: tcgen05.ld -> recurrence -> FP32 master of
+//                  Y_{i+1}, bf16 hi/lo B operand of the next step, FP64
+//                  output for columns that finish at this step.
+// Every mbarrier wait is bounded (globaltimer); on timeout the CTA sets an
+// error word, lets the other roles drain and releases its TMEM.
+//
+// "Defect" form (iterative refinement of the filter, not in the paper):
+// for Ritz vectors Y with values Lambda and residual block R = HY - Y
+// Lambda, the filtered block is p(H) Y = Y psi(Lambda) + D, where psi is
+// the scalar recurrence applied to each Ritz value and D follows the same
+// three-term recurrence driven by R:
+//     D_0 = 0,  D_1 = a_0 R,
+//     D_{i+1} = a_i (H D_i - c D_i) + b_i D_{i-1} + a_i psi_i(lambda_j) R_j.
+// D is of the size of the residual, so computing it in split precision
+// leaves an error of (split precision) x (residual) instead of the split
+// precision itself; Y psi(Lambda) is formed in FP64.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "common.cuh"
 
-struct TcFilterState {};
+namespace {
 
-int tc_filter_supported(chfsi_ctx*) { return 0; }
-void tc_filter_prepare(chfsi_ctx*, const double2*, int) {
-  throw ChfsiError{CHFSI_ENOTSUP, "tensor-core filter not built"};
+constexpr int BM = 128;        // tile rows (UMMA M)
+constexpr int BK = 64;         // K block (one 128-byte swizzle row of bf16)
+constexpr int NTHREADS = 256;
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s per wait
+
+// ------------------------------------------------------------ PTX -------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
-void tc_filter_run(chfsi_ctx*, const double2*, int, int, const double2*, const int*, double,
-                   double, double, double2*) {
-  throw ChfsiError{CHFSI_ENOTSUP, "tensor-core filter not built"};
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
-void tc_filter_release(chfsi_ctx*) {}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait.  Returns false (and raises the CTA abort flag and the
+// global error word) when the phase did not complete in time, or when
+// another role of this CTA has already aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_sh,
+                                          int* err, int code) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_sh) return false;
+    if (globaltimer() - t0 > WAIT_NS) {
+      *abort_sh = 1;
+      atomicExch(err, code);
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(dst_smem)),
+               "r"(ncols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor, K-major operand with 128-byte swizzle:
+// start address >> 4 (bits 0-13), leading-dimension offset 16 B (unused
+// for this layout), stride offset 1024 B between 8-row groups (bits
+// 32-45), descriptor version 1 (bit 46), swizzle mode 2 = 128 B (61-63).
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+         ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
+// (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at
+// bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(x);
+  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// ------------------------------------------------------------ kernel ----
+struct StepParams {
+  int n;          // rows of H
+  int ka;         // active complex columns in this launch
+  int P;          // row pitch (elements) of the A and B operand arrays
+  int ntile;      // N of a tile (real columns, multiple of 16)
+  int stages;
+  int kblocks;    // ceil(2n / 64)
+  uint32_t tmem_cols;
+  float a, c, b;  // recurrence scalars of this step
+  const float2* cur;    // FP32 master of Y_i (n x ka, ld n), active columns
+  const float2* prev;   // FP32 master of Y_{i-1} (null when b == 0)
+  const double2* R;     // defect forcing block (null in plain form)
+  const double* fR;     // per-column forcing coefficient a_i psi_i(lambda_j)
+  float2* next;         // FP32 master of Y_{i+1}
+  __nv_bfloat16* bh;    // next B operand, hi (row 2j = column 2j of B), offset
+  __nv_bfloat16* bl;    //   to the active start
+  double2* out;         // finished columns (c < fin_end) in FP64
+  int fin_end;
+  int* err;
+};
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+tc_filter_step_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+                      const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
+                      int b_row0, StepParams p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int N = p.ntile;
+  const uint32_t a_bytes = BM * BK * 2;        // 16 KB per A split
+  const uint32_t b_bytes = (uint32_t)N * BK * 2;
+  const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
+  uint64_t* bars = (uint64_t*)(smem + (size_t)p.stages * stage_bytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + p.stages;
+  uint64_t* accf = bars + 2 * p.stages;
+  uint32_t* tmem_slot = (uint32_t*)(accf + 1);
+  volatile int* abort_sh = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM;
+  const int n0 = blockIdx.x * N;  // first real column of this tile (active-relative)
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    *abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) tmem_alloc(tmem_slot, p.tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    int issued = 0;
+    for (int kb = 0; kb < p.kblocks; ++kb) {
+      const int s = kb % p.stages;
+      const uint32_t ph = (uint32_t)(kb / p.stages) & 1u;
+      if (!mbar_wait(&empty[s], ph ^ 1u, abort_sh, p.err, 1)) break;
+      unsigned char* st = smem + (size_t)s * stage_bytes;
+      mbar_arrive_expect_tx(&full[s], stage_bytes);
+      tma_load_2d(st, &mAh, &full[s], kb * BK, m0);
+      tma_load_2d(st + a_bytes, &mAl, &full[s], kb * BK, m0);
+      tma_load_2d(st + 2 * a_bytes, &mBh, &full[s], kb * BK, b_row0 + n0);
+      tma_load_2d(st + 2 * a_bytes + b_bytes, &mBl, &full[s], kb * BK, b_row0 + n0);
+      issued = kb + 1;
+    }
+    if (*abort_sh) {
+      // Let the copies still in flight land before the CTA releases its
+      // shared memory (bounded wait on each stage's last armed phase).
+      for (int kb = (issued > p.stages ? issued - p.stages : 0); kb < issued; ++kb) {
+        const uint64_t t0 = globaltimer();
+        while (!mbar_try_wait(&full[kb % p.stages], (uint32_t)(kb / p.stages) & 1u) &&
+               globaltimer() - t0 < WAIT_NS) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    const uint32_t idesc = idesc_bf16(BM, N);
+    bool ok = true;
+    for (int kb = 0; kb < p.kblocks && ok; ++kb) {
+      const int s = kb % p.stages;
+      const uint32_t ph = (uint32_t)(kb / p.stages) & 1u;
+      if (!mbar_wait(&full[s], ph, abort_sh, p.err, 2)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t sa = smem_u32(smem + (size_t)s * stage_bytes);
+      const uint64_t dAh = desc_sw128(sa), dAl = desc_sw128(sa + a_bytes);
+      const uint64_t dBh = desc_sw128(sa + 2 * a_bytes), dBl = desc_sw128(sa + 2 * a_bytes + b_bytes);
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint64_t adv = (uint64_t)((kk * 32) >> 4);  // 16 bf16 = 32 B along K
+        const uint32_t acc0 = (kb > 0 || kk > 0) ? 1u : 0u;
+        umma_bf16(tmem, dAh + adv, dBh + adv, idesc, acc0);
+        umma_bf16(tmem, dAh + adv, dBl + adv, idesc, 1u);
+        umma_bf16(tmem, dAl + adv, dBh + adv, idesc, 1u);
+      }
+      umma_commit(&empty[s]);
+    }
+    if (ok) umma_commit(accf);
+  } else if (warp >= 4) {
+    // ---------------- epilogue ----------------
+    const int q = warp & 3;
+    const int row = m0 + q * 32 + lane;
+    const bool ok = mbar_wait(accf, 0u, abort_sh, p.err, 3);
+    tc_fence_after();
+    if (ok) {
+      const int n = p.n;
+      const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
+      for (int c0 = 0; c0 < N; c0 += 16) {
+        float v[16];
+        __syncwarp();
+        tmem_ld16(tq + (uint32_t)c0, v);  // warp-collective: all lanes take part
+        if (row >= n) continue;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int j = (n0 + c0) / 2 + t;  // active-relative complex column
+          if (j >= p.ka) break;
+          const size_t e = (size_t)row + (size_t)j * n;
+          const float2 cu = p.cur[e];
+          float re = p.a * (v[2 * t] - p.c * cu.x);
+          float im = p.a * (v[2 * t + 1] - p.c * cu.y);
+          if (p.prev) {
+            const float2 pv = p.prev[e];
+            re = fmaf(p.b, pv.x, re);
+            im = fmaf(p.b, pv.y, im);
+          }
+          if (p.R) {
+            const double f = p.fR[j];
+            const double2 rr = p.R[e];
+            re += (float)(f * rr.x);
+            im += (float)(f * rr.y);
+          }
+          p.next[e] = make_float2(re, im);
+          __nv_bfloat16 h, l;
+          const size_t r0 = (size_t)(2 * j) * p.P, r1 = r0 + p.P;
+          split_bf16(re, h, l);
+          p.bh[r0 + row] = h;  p.bl[r0 + row] = l;          // column 2j, top:   Yr
+          p.bh[r1 + n + row] = h;  p.bl[r1 + n + row] = l;  // column 2j+1, bottom: Yr
+          split_bf16(im, h, l);
+          p.bh[r1 + row] = h;  p.bl[r1 + row] = l;          // column 2j+1, top: Yi
+          split_bf16(-im, h, l);
+          p.bh[r0 + n + row] = h;  p.bl[r0 + n + row] = l;  // column 2j, bottom: -Yi
+          if (j < p.fin_end) p.out[e] = make_double2((double)re, (double)im);
+        }
+      }
+    }
+    tc_fence_before();
+  }
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    tmem_dealloc(tmem, p.tmem_cols);
+  }
+}
+
+// ------------------------------------------------- operand preparation --
+// Row r of A = [Re H[r, :] | Im H[r, :]]; for Hermitian H, H[r, x] =
+// conj(H[x, r]), so row r is read from column r (contiguous).
+__global__ void repack_h_kernel(int n, int P, const double2* __restrict__ H,
+                                __nv_bfloat16* __restrict__ Ah, __nv_bfloat16* __restrict__ Al) {
+  const int r = blockIdx.y;
+  const double2* col = H + (size_t)r * n;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < 2 * n; x += gridDim.x * blockDim.x) {
+    const double v = (x < n) ? col[x].x : -col[x - n].y;
+    const __nv_bfloat16 h = __double2bfloat16(v);
+    const __nv_bfloat16 l = __double2bfloat16(v - (double)__bfloat162float(h));
+    Ah[(size_t)r * P + x] = h;
+    Al[(size_t)r * P + x] = l;
+  }
+}
+
+// B operand + FP32 master of an n x k block.  Plain form: src = Y0 (scale
+// 1).  Defect form: src = R, scale = a_0 (D_1 = a_0 R).  Columns below
+// fin_end are also written to out (FP64) when out is not null.
+__global__ void split_block_kernel(int n, int k, int P, const double2* __restrict__ src,
+                                   double scale, float2* __restrict__ master,
+                                   __nv_bfloat16* __restrict__ bh, __nv_bfloat16* __restrict__ bl,
+                                   double2* __restrict__ out, int fin_end) {
+  const int j = blockIdx.y;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const size_t e = (size_t)r + (size_t)j * n;
+    const double2 s = src[e];
+    const float re = (float)(scale * s.x), im = (float)(scale * s.y);
+    master[e] = make_float2(re, im);
+    if (out && j < fin_end) out[e] = make_double2(scale * s.x, scale * s.y);
+    __nv_bfloat16 h, l;
+    const size_t r0 = (size_t)(2 * j) * P, r1 = r0 + P;
+    split_bf16(re, h, l);
+    bh[r0 + r] = h;  bl[r0 + r] = l;
+    bh[r1 + n + r] = h;  bl[r1 + n + r] = l;
+    split_bf16(im, h, l);
+    bh[r1 + r] = h;  bl[r1 + r] = l;
+    split_bf16(-im, h, l);
+    bh[r0 + n + r] = h;  bl[r0 + n + r] = l;
+  }
+}
+
+// psi[i * k + j] = psi_i(lambda_j): the filter's scalar recurrence on each
+// Ritz value (psi_0 = 1, psi_1 = a_0 (lambda - c), psi_{i+1} = a_i (lambda -
+// c) psi_i + b_i psi_{i-1}).  coef = {a_0, (a_i, b_i) for i >= 1}.
+__global__ void psi_table_kernel(int k, int m, const double* __restrict__ lam, double c,
+                                 const double* __restrict__ coef, double* __restrict__ psi) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= k) return;
+  const double t = lam[j] - c;
+  double p0 = 1.0, p1 = coef[0] * t;
+  psi[j] = p0;
+  if (m >= 1) psi[(size_t)k + j] = p1;
+  for (int i = 1; i < m; ++i) {
+    const double p2 = coef[2 * i - 1] * t * p1 + coef[2 * i] * p0;
+    psi[(size_t)(i + 1) * k + j] = p2;
+    p0 = p1;
+    p1 = p2;
+  }
+}
+
+// Y'_j = Y_j psi_{m_j}(lambda_j) + D_j (FP64), in place on D.
+__global__ void defect_combine_kernel(int n, int k, const double2* __restrict__ Y,
+                                      const int* __restrict__ deg, const double* __restrict__ psi,
+                                      double2* __restrict__ D) {
+  const int j = blockIdx.y;
+  const double f = psi[(size_t)deg[j] * k + j];
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const size_t e = (size_t)r + (size_t)j * n;
+    const double2 y = Y[e];
+    double2 d = D[e];
+    d.x = fma(f, y.x, d.x);
+    d.y = fma(f, y.y, d.y);
+    D[e] = d;
+  }
+}
+
+// out[i * k + j] = psi[i * k + j] * a[i]
+__global__ void scale_rows_kernel(int rows, int k, const double* __restrict__ psi,
+                                  const double* __restrict__ a, double* __restrict__ out) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= (size_t)rows * k) return;
+  out[t] = psi[t] * a[t / k];
+}
+
+// ------------------------------------------------------------ host ------
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    CHFSI_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                                    cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p)
+      throw ChfsiError{CHFSI_ENOTSUP, "cuTensorMapEncodeTiled unavailable"};
+    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 2-D bf16 map over a (rows x cols) array with row pitch P elements; box
+// (64 x box_rows), 128-byte swizzle, zero fill outside the extent.
+CUtensorMap make_map(const void* base, int cols, int rows, int P, int box_rows) {
+  CUtensorMap m;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)P * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = get_encode()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base),
+                            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    throw ChfsiError{CHFSI_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")"};
+  return m;
+}
+
+// Tile N (real columns, multiple of 16, <= 256) for `cols` active real
+// columns and `mtiles` row tiles: fewest waves over the SMs, then the
+// smallest per-CTA width (a fixed per-tile cost of 32 columns is added).
+int pick_ntile(int cols, int mtiles, int sms) {
+  int best = 256;
+  double best_cost = 1e300;
+  for (int N = 32; N <= 256; N += 16) {
+    const int tiles = mtiles * ((cols + N - 1) / N);
+    const int waves = (tiles + sms - 1) / sms;
+    const double cost = (double)waves * (N + 32);
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = N;
+    }
+  }
+  return best;
+}
+
+}  // namespace
+
+struct TcFilterState {
+  int n = 0, P = 0, kcap = 0;
+  __nv_bfloat16* A = nullptr;  // A_hi then A_lo, n x P each
+  __nv_bfloat16* B = nullptr;  // 2 buffers x (hi, lo) x (2 kcap) x P
+  float2* M = nullptr;         // 3 FP32 masters, n x kcap each
+  int* err = nullptr;
+  size_t a_elems = 0, b_elems = 0;
+  bool attr_set = false;
+};
+
+int tc_filter_supported(chfsi_ctx* ctx) { return ctx->cc_major == 10 && ctx->cc_minor == 3; }
+
+void tc_filter_release(chfsi_ctx* ctx) {
+  TcFilterState* s = ctx->tc;
+  if (!s) return;
+  cudaFree(s->A);
+  cudaFree(s->B);
+  cudaFree(s->M);
+  cudaFree(s->err);
+  delete s;
+  ctx->tc = nullptr;
+}
+
+static void tc_reserve(chfsi_ctx* ctx, int n, int k) {
+  if (!ctx->tc) ctx->tc = new TcFilterState();
+  TcFilterState* s = ctx->tc;
+  const int P = (2 * n + 7) / 8 * 8;  // 16-byte row pitch for TMA
+  if (s->n != n || s->P != P || !s->A) {
+    cudaFree(s->A);
+    s->A = nullptr;
+    s->a_elems = (size_t)n * P;
+    CHFSI_CUDA_TRY(cudaMalloc(&s->A, sizeof(__nv_bfloat16) * 2 * s->a_elems));
+    s->n = n;
+    s->P = P;
+    s->kcap = 0;
+  }
+  if (k > s->kcap) {
+    cudaFree(s->B);
+    cudaFree(s->M);
+    s->B = nullptr;
+    s->M = nullptr;
+    s->b_elems = (size_t)2 * k * P;
+    CHFSI_CUDA_TRY(cudaMalloc(&s->B, sizeof(__nv_bfloat16) * 4 * s->b_elems));
+    CHFSI_CUDA_TRY(cudaMalloc(&s->M, sizeof(float2) * 3 * (size_t)n * k));
+    s->kcap = k;
+  }
+  if (!s->err) {
+    CHFSI_CUDA_TRY(cudaMalloc(&s->err, sizeof(int)));
+    CHFSI_CUDA_TRY(cudaMemsetAsync(s->err, 0, sizeof(int), ctx->stream));
+  }
+  if (!s->attr_set) {
+    CHFSI_CUDA_TRY(cudaFuncSetAttribute(tc_filter_step_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    s->attr_set = true;
+  }
+}
+
+void tc_filter_prepare(chfsi_ctx* ctx, const double2* H, int n) {
+  tc_reserve(ctx, n, 1);
+  TcFilterState* s = ctx->tc;
+  dim3 grid((2 * n + 255) / 256, n);
+  repack_h_kernel<<<grid, 256, 0, ctx->stream>>>(n, s->P, H, s->A, s->A + s->a_elems);
+  chfsi_check_launch("repack_h");
+}
+
+namespace {
+
+struct TcRun {
+  chfsi_ctx* ctx;
+  TcFilterState* s;
+  int n, k;
+  CUtensorMap mAh, mAl;
+  __nv_bfloat16* bh(int buf) { return s->B + (size_t)buf * 2 * s->b_elems; }
+  __nv_bfloat16* bl(int buf) { return bh(buf) + s->b_elems; }
+  float2* master(int i) { return s->M + (size_t)(i % 3) * n * k; }
+};
+
+void launch_step(TcRun& R, int bufB_in, int bufB_out, int s_col, int ka, float a, float c,
+                 float b, const float2* cur, const float2* prev, const double2* Rsrc,
+                 const double* fR, float2* next, double2* out, int fin_end) {
+  TcFilterState* s = R.s;
+  const int n = R.n, P = s->P;
+  const int cols = 2 * ka;
+  const int mtiles = (n + BM - 1) / BM;
+  const int N = pick_ntile(cols, mtiles, R.ctx->sm_count);
+  const uint32_t stage_bytes = 2u * BM * BK * 2 + 2u * N * BK * 2;
+  int stages = (int)((220u * 1024u) / stage_bytes);
+  stages = std::max(2, std::min(stages, 6));
+  const size_t smem = 1024 + (size_t)stages * stage_bytes + 8 * (2 * stages + 1) + 16;
+  uint32_t tcols = 32;
+  while ((int)tcols < N) tcols <<= 1;
+  CUtensorMap mBh = make_map(R.bh(bufB_in), 2 * n, 2 * R.k, P, N);
+  CUtensorMap mBl = make_map(R.bl(bufB_in), 2 * n, 2 * R.k, P, N);
+  StepParams p;
+  p.n = n;
+  p.ka = ka;
+  p.P = P;
+  p.ntile = N;
+  p.stages = stages;
+  p.kblocks = (2 * n + BK - 1) / BK;
+  p.tmem_cols = tcols;
+  p.a = a;
+  p.c = c;
+  p.b = b;
+  p.cur = cur + (size_t)s_col * n;
+  p.prev = prev ? prev + (size_t)s_col * n : nullptr;
+  p.R = Rsrc ? Rsrc + (size_t)s_col * n : nullptr;
+  p.fR = fR ? fR + s_col : nullptr;
+  p.next = next + (size_t)s_col * n;
+  p.bh = R.bh(bufB_out) + (size_t)(2 * s_col) * P;
+  p.bl = R.bl(bufB_out) + (size_t)(2 * s_col) * P;
+  p.out = out + (size_t)s_col * n;
+  p.fin_end = fin_end;
+  p.err = s->err;
+  dim3 grid((cols + N - 1) / N, mtiles);
+  tc_filter_step_kernel<<<grid, NTHREADS, smem, R.ctx->stream>>>(R.mAh, R.mAl, mBh, mBl,
+                                                                 2 * s_col, p);
+  chfsi_check_launch("tc_filter_step");
+}
+
+void check_err(chfsi_ctx* ctx) {
+  int* h = (int*)pinned_get(ctx, 64);
+  CHFSI_CUDA_TRY(cudaMemcpyAsync(h, ctx->tc->err, sizeof(int), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+  CHFSI_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  if (*h) {
+    CHFSI_CUDA_TRY(cudaMemsetAsync(ctx->tc->err, 0, sizeof(int), ctx->stream));
+    throw ChfsiError{CHFSI_ETIMEOUT, "tensor-core filter: pipeline wait timed out (code " +
+                                         std::to_string(*h) + ")"};
+  }
+}
+
+// Shared driver of both forms.  Plain: Y_0 = Y0, recurrence of Alg. 2.
+// Defect: D_0 = 0, D_1 = a_0 R, forcing a_i psi_i R; output D (combined
+// with Y psi by the caller).
+void run_filter(chfsi_ctx* ctx, const double2* H, int n, int k, const double2* src,
+                const double2* Rdef, const double* psi_dev, const int* deg, double lam1,
+                double c, double e, double2* out) {
+  tc_reserve(ctx, n, k);
+  TcFilterState* s = ctx->tc;
+  // Rebuilt on every call: the same device buffer may hold a new H.
+  tc_filter_prepare(ctx, H, n);
+  TcRun R{ctx, s, n, k, {}, {}};
+  R.mAh = make_map(s->A, 2 * n, n, s->P, BM);
+  R.mAl = make_map(s->A + s->a_elems, 2 * n, n, s->P, BM);
+  cudaStream_t st = ctx->stream;
+  const bool defect = Rdef != nullptr;
+  const int mk = deg[k - 1];
+  const double sigma1 = e / (lam1 - c);
+  int sidx = (int)(std::upper_bound(deg, deg + k, 1) - deg);
+  // Y_1 (plain) or D_1 (defect).
+  if (!defect) {
+    split_block_kernel<<<dim3((n + 255) / 256, k), 256, 0, st>>>(n, k, s->P, src, 1.0,
+                                                                 R.master(0), R.bh(0), R.bl(0),
+                                                                 nullptr, 0);
+    chfsi_check_launch("split_block");
+    launch_step(R, 0, 1, 0, k, (float)(sigma1 / e), (float)c, 0.f, R.master(0), nullptr,
+                nullptr, nullptr, R.master(1), out, sidx);
+  } else {
+    split_block_kernel<<<dim3((n + 255) / 256, k), 256, 0, st>>>(n, k, s->P, Rdef, sigma1 / e,
+                                                                 R.master(1), R.bh(1), R.bl(1),
+                                                                 out, sidx);
+    chfsi_check_launch("split_block");
+  }
+  double sigma = sigma1;
+  for (int i = 1; i < mk; ++i) {
+    const double sn = 1.0 / (2.0 / sigma1 - sigma);
+    const int s_new = (int)(std::upper_bound(deg, deg + k, i + 1) - deg);
+    const float2* prev = (i == 1 && defect) ? nullptr : R.master(i - 1);
+    launch_step(R, i & 1, (i + 1) & 1, sidx, k - sidx, (float)(2.0 * sn / e), (float)c,
+                (float)(-sn * sigma), R.master(i), prev, defect ? Rdef : nullptr,
+                defect ? psi_dev + (size_t)i * k : nullptr, R.master(i + 1), out, s_new - sidx);
+    sigma = sn;
+    sidx = s_new;
+  }
+  check_err(ctx);
+}
+
+}  // namespace
+
+void tc_filter_run(chfsi_ctx* ctx, const double2* H, int n, int k, const double2* Y0,
+                   const int* deg_host, double lam1, double c, double e, double2* Yout) {
+  run_filter(ctx, H, n, k, Y0, nullptr, nullptr, deg_host, lam1, c, e, Yout);
+}
+
+// Defect form: Y (Ritz vectors, degree-sorted), R = HY - Y Lambda (same
+// order), lam (Ritz values, device, same order), deg_dev (device copy of
+// the degrees).  Yout = p(H) Y per column.
+void tc_filter_run_defect(chfsi_ctx* ctx, const double2* H, int n, int k, const double2* Y,
+                          const double2* Rres, const double* lam, const int* deg_host,
+                          const int* deg_dev, double lam1, double c, double e, double2* Yout) {
+  const int mk = deg_host[k - 1];
+  // Recurrence coefficients a_0; (a_i, b_i) i >= 1, and the psi table whose
+  // row i holds the forcing coefficient a_i psi_i(lambda_j) for step i.
+  std::vector<double> coef(2 * mk + 1, 0.0);
+  const double sigma1 = e / (lam1 - c);
+  coef[0] = sigma1 / e;
+  double sigma = sigma1;
+  for (int i = 1; i < mk; ++i) {
+    const double sn = 1.0 / (2.0 / sigma1 - sigma);
+    coef[2 * i - 1] = 2.0 * sn / e;
+    coef[2 * i] = -sn * sigma;
+    sigma = sn;
+  }
+  double* dcoef = (double*)ws_get(ctx, "tc_coef", sizeof(double) * coef.size());
+  double* psi = (double*)ws_get(ctx, "tc_psi", sizeof(double) * (size_t)(mk + 1) * k);
+  double* fR = (double*)ws_get(ctx, "tc_fR", sizeof(double) * (size_t)(mk + 1) * k);
+  CHFSI_CUDA_TRY(cudaMemcpyAsync(dcoef, coef.data(), sizeof(double) * coef.size(),
+                                 cudaMemcpyHostToDevice, ctx->stream));
+  psi_table_kernel<<<(k + 127) / 128, 128, 0, ctx->stream>>>(k, mk, lam, c, dcoef, psi);
+  chfsi_check_launch("psi_table");
+  // forcing coefficients fR[i][j] = a_i psi_i(lambda_j)
+  std::vector<double> ai(mk + 1, 0.0);
+  for (int i = 1; i < mk; ++i) ai[i] = coef[2 * i - 1];
+  double* dai = (double*)ws_get(ctx, "tc_ai", sizeof(double) * (mk + 1));
+  CHFSI_CUDA_TRY(cudaMemcpyAsync(dai, ai.data(), sizeof(double) * (mk + 1),
+                                 cudaMemcpyHostToDevice, ctx->stream));
+  scale_rows_kernel<<<(unsigned)(((size_t)(mk + 1) * k + 255) / 256), 256, 0, ctx->stream>>>(
+      mk + 1, k, psi, dai, fR);
+  chfsi_check_launch("scale_rows");
+  run_filter(ctx, H, n, k, Y, Rres, fR, deg_host, lam1, c, e, Yout);
+  defect_combine_kernel<<<dim3((n + 255) / 256, k), 256, 0, ctx->stream>>>(n, k, Y, deg_dev,
+                                                                          psi, Yout);
+  chfsi_check_launch("defect_combine");
+}

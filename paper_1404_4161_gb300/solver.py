@@ -113,6 +113,15 @@ class Chfsi:
                                           precision))
         return out
 
+    def filter_refine(self, Hc, Yc, Rc, ritz, degrees, lam1, c, e):
+        k, n = Yc.shape
+        out = torch.empty_like(Yc)
+        d = (C.c_int * max(k, 1))(*[int(x) for x in degrees])
+        self._check(self.lib.chfsi_filter_refine(self.ctx, _ptr(Hc), n, k, _ptr(Yc), _ptr(Rc),
+                                                 _ptr(ritz), C.cast(d, C.c_void_p), lam1, c, e,
+                                                 _ptr(out)))
+        return out
+
     def orthonormalize(self, Yc, Lc=None):
         k, n = Yc.shape
         nl = 0 if Lc is None else Lc.shape[0]
