@@ -39,6 +39,8 @@ extern "C" {
 #define CHFSI_ETIMEOUT 6    /* a bounded device wait gave up                */
 #define CHFSI_ECUDA 7       /* CUDA / cuSOLVER runtime error                */
 #define CHFSI_ENOTSUP 8     /* configuration not supported on this device   */
+#define CHFSI_ETOOBIG 9     /* n*k above the static scratch of               */
+                            /* chfsi_filter_static (CHFSI_FILTER_STATIC_MAX_NK) */
 
 /* Arithmetic of the filter (the other steps always run in FP64). */
 #define CHFSI_PREC_FP64 0   /* complex FP64 filter on the FP64 pipe          */
@@ -209,6 +211,40 @@ int chfsi_residuals(chfsi_ctx* ctx, int n, int k, const double* HY,
  * degree.  ritz, resid: k doubles; degrees: k ints (all device). */
 int chfsi_degrees(chfsi_ctx* ctx, int k, const double* ritz, const double* resid,
                   double c, double e, double tol, int n_wanted, int* degrees);
+
+/* ---- filter without device allocation ---------------------------------- */
+
+/* Largest n*k accepted by chfsi_filter_static. */
+#define CHFSI_FILTER_STATIC_MAX_NK 262144
+
+/* The FP64 Chebyshev filter of chfsi_filter (same arguments and result as
+ * precision CHFSI_PREC_FP64), for callers that cannot allocate device
+ * memory on the call path: applications that reserve the whole device for
+ * their own memory pool at start-up, so a further cudaMalloc fails or
+ * fragments that pool, and latency-bound code that cannot accept the
+ * implicit device synchronisation of cudaMalloc / cudaFree.  The paper has
+ * no counterpart; this is a deployment variant of the filter step.
+ *
+ * It needs no context and allocates nothing: its three recurrence buffers
+ * are one static device array of 3 * CHFSI_FILTER_STATIC_MAX_NK complex128
+ * elements (12 MiB) that every GPU which loads this library keeps until the
+ * process exits.  Work is issued on `stream` (a cudaStream_t; NULL = the
+ * legacy default stream) and is stream-ordered; the call returns without
+ * synchronising.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the one array: calls whose
+ * work overlaps on the GPU (different streams, or different host threads)
+ * race and give wrong results; serialise them.  The buffers are fully
+ * written before they are read, so no earlier contents leak into a result.
+ *
+ * Returns CHFSI_ETOOBIG when n * k > CHFSI_FILTER_STATIC_MAX_NK (no work is
+ * issued), CHFSI_EINVAL for the argument errors of chfsi_filter, CHFSI_ECUDA
+ * when the address lookup or a launch fails. */
+int chfsi_filter_static(const double* H, int n, int k, const double* Y0,
+                        const int* degrees_host, double lam1, double c, double e,
+                        double* Y, void* stream);
 
 /* ---- learned degree predictor (not in the paper) ---------------------- */
 

@@ -11,7 +11,8 @@ import os
 
 from .build import LIB
 
-OK, EINVAL, ENOMEM, ENOCONV, EBREAKDOWN, ENAN, ETIMEOUT, ECUDA, ENOTSUP = range(9)
+OK, EINVAL, ENOMEM, ENOCONV, EBREAKDOWN, ENAN, ETIMEOUT, ECUDA, ENOTSUP, ETOOBIG = range(10)
+FILTER_STATIC_MAX_NK = 262144
 PREC_FP64, PREC_MIXED, PREC_TC = 0, 1, 2
 SPLIT_BF16X3, SPLIT_FP16X3 = 0, 1
 DEG_ANALYTIC, DEG_MLP = 0, 1
@@ -71,6 +72,8 @@ _SIGS = {
     "chfsi_residuals": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P, C.c_double, _P]),
     "chfsi_degrees": (C.c_int, [_P, C.c_int, _P, _P, C.c_double, C.c_double, C.c_double,
                                 C.c_int, _P]),
+    "chfsi_filter_static": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_double, C.c_double,
+                                      C.c_double, _P, _P]),
     "chfsi_mlp_set_params": (C.c_int, [_P, _P]),
     "chfsi_mlp_get_params": (C.c_int, [_P, _P]),
     "chfsi_mlp_forward": (C.c_int, [_P, C.c_int, _P, _P]),

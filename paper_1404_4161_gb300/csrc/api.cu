@@ -559,6 +559,7 @@ const char* chfsi_strerror(int code) {
     case CHFSI_ETIMEOUT: return "device wait timed out";
     case CHFSI_ECUDA: return "CUDA runtime error";
     case CHFSI_ENOTSUP: return "not supported on this device";
+    case CHFSI_ETOOBIG: return "n*k exceeds the static scratch of chfsi_filter_static";
     default: return "unknown error";
   }
 }

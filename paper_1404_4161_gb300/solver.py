@@ -172,3 +172,19 @@ class Chfsi:
         self._check(self.lib.chfsi_mlp_train_step(self.ctx, x.shape[0], _ptr(x), _ptr(target),
                                                   lr, _ptr(g), C.byref(loss)))
         return float(loss.value), g
+
+
+def filter_static(Hc, Y0c, degrees, lam1, c, e, out=None):
+    """chfsi_filter_static on torch's current stream: the FP64 filter with
+    its scratch in the library's static device array (no allocation by
+    the library; ``out`` may be passed in to avoid one by torch).
+    Returns (out, return code)."""
+    lib = L.lib()
+    k, n = Y0c.shape
+    if out is None:
+        out = torch.empty_like(Y0c)
+    d = (C.c_int * max(k, 1))(*[int(x) for x in degrees])
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = lib.chfsi_filter_static(_ptr(Hc), n, k, _ptr(Y0c), C.cast(d, C.c_void_p), lam1, c, e,
+                                 _ptr(out), C.c_void_p(stream))
+    return out, rc
