@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--fp64-compare", type=int, default=0,
                     help="also time the plain FP64 path on this many problems")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
 
@@ -313,7 +314,7 @@ def main():
         s64.close()
 
     cpu = None
-    if rank == 0 and ws == 1:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and length >= 2:
         Hh2 = [Hcs[0].t().cpu().numpy(), Hcs[1].t().cpu().numpy()]
         cpu = cpu_baseline_sample(Hh2, nev, nex, cfg.tol, X0, length)
 

@@ -74,15 +74,13 @@ def haar_unitary(n: int, rng: np.random.Generator, device=None):
     """Haar-distributed n x n unitary (numpy array, or torch tensor on
     ``device`` when one is given)."""
     z = ginibre(n, n, rng)
+    q, r = np.linalg.qr(z)
+    d = np.diag(r)
+    q = q * (d / np.abs(d))[None, :]
     if device is None:
-        q, r = np.linalg.qr(z)
-        d = np.diag(r)
-        return q * (d / np.abs(d))[None, :]
+        return q
     import torch
-    zt = torch.from_numpy(z).to(device)
-    q, r = torch.linalg.qr(zt)
-    d = torch.diagonal(r)
-    return q * (d / d.abs()).unsqueeze(0)
+    return torch.from_numpy(q).to(device)
 
 
 def two_band_spectrum(n: int, n_low: int, low, bulk, rng) -> np.ndarray:
