@@ -59,8 +59,18 @@ def test_features_and_labels():
     x = mlp.features([-2.0, 0.5], [1e-4, 1e-2], 1.0, 2.0, -3.0, 7)
     assert np.allclose(x[0], [-1.5, -0.4, np.arccosh(1.5), -2.0, 0.7])
     assert x[1, 2] == 0.0
-    # residual 1e-2 -> 1e-6 in 10 degrees: kappa = ln(1e4)/10; need ln(1e8)/kappa = 20
-    lab = mlp.degree_label([1e-2], [1e-6], [10], 1e-10)
-    assert lab[0] == 20
-    # no decay -> the cap
-    assert mlp.degree_label([1e-2], [1e-2], [10], 1e-10)[0] == mlp.DEG_HI
+    # t = -2: acosh 2 = 1.316958; residual 1e-2 -> 1e-6 in 10 degrees gives
+    # kappa = ln(1e4)/10 = 0.921034, ratio 0.699364
+    y = mlp.decay_label([-3.0], [1e-2], [1e-6], [10], 1.0, 2.0)
+    assert abs(y[0] - 0.921034037 / 1.316957897) < 1e-8
+    assert mlp.decay_label([-3.0], [1e-2], [1e-2], [10], 1.0, 2.0)[0] == mlp.Y_LO
+    # degree from the ratio: ln(1e-2/1e-10) / (1.316958 * 0.5) = 27.98 -> 28 + 2
+    m = mlp.degrees_from_prediction([0.5], [-3.0], [1e-2], 1.0, 2.0, 1e-10, extra=2)
+    assert m[0] == 30
+    # a ratio of 1 reproduces the analytic rule (with the same margin)
+    import oracle
+    mr = oracle.degree_rule(np.array([-3.0]), np.array([1e-2]), 1.0, 2.0, 1e-10, 60, deg_extra=2)
+    assert mlp.degrees_from_prediction([1.0], [-3.0], [1e-2], 1.0, 2.0, 1e-10, extra=2)[0] == mr[0]
+    # inside the damped interval -> the cap; tiny residual -> the floor
+    assert mlp.degrees_from_prediction([1.0], [2.0], [1e-2], 1.0, 2.0, 1e-10)[0] == mlp.DEG_HI
+    assert mlp.degrees_from_prediction([1.0], [-3.0], [1e-12], 1.0, 2.0, 1e-10)[0] == mlp.DEG_LO
