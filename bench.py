@@ -43,10 +43,13 @@ def parse():
     ap.add_argument("--precision", choices=["tc", "mixed", "fp64"], default="tc")
     ap.add_argument("--n", type=int, default=None, help="override n (smaller test runs)")
     ap.add_argument("--length", type=int, default=None)
-    ap.add_argument("--fp64-compare", type=int, default=0,
+    ap.add_argument("--fp64-compare", type=int, default=2,
                     help="also time the plain FP64 path on this many problems")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--degrees", choices=["learned", "analytic"], default="learned")
+    ap.add_argument("--train-length", type=int, default=4,
+                    help="problems in the (separate) training sequence of the degree MLP")
     return ap.parse_args()
 
 
@@ -215,8 +218,27 @@ def main():
     torch.cuda.synchronize()
 
     prec = {"tc": L.PREC_TC, "mixed": L.PREC_MIXED, "fp64": L.PREC_FP64}[args.precision]
-    s = Chfsi(precision=prec)
+    s = Chfsi(precision=prec, profile=1)
     stream = torch.cuda.current_stream()
+    train_info = None
+    if args.degrees == "learned":
+        # The degree MLP learns from traces the method itself generates, on a
+        # separate training sequence (same generator, other seed); untimed.
+        from paper_1404_4161_gb300 import learned
+        Ht, _ = config_sequence(cfg, 14044161 + 2700, length=args.train_length, n=n, device=dev)
+        Htc = [colmajor(h) for h in Ht]
+        del Ht
+        s.trace_enable(1 << 20)
+        Xt = colmajor(torch.from_numpy(random_block(n, k, 14044161 + 2750)).to(dev))
+        s.solve_sequence(Htc, nev, nex, Xt, cfg.tol)
+        xs, ys = learned.dataset(s)
+        losses = learned.train(s, xs, ys, steps=3000, lr=2e-3)
+        s.trace_enable(0)
+        del Htc, Xt
+        torch.cuda.empty_cache()
+        train_info = {"rows": int(xs.shape[0]), "steps": 3000, "loss0": losses[0],
+                      "loss": losses[-1], "train_problems": args.train_length}
+        s.set_opts(degree_model=L.DEG_MLP)
 
     def step():
         Xc = X0c.clone()
@@ -260,24 +282,42 @@ def main():
     filt_launch = sum(x["filter_launches"] for x in last)
     launches = sum(sum(x["launches"] for x in sts) for sts in stats_all)
     lowp_flops = sum(8.0 * n * n * x["col_degrees_lowp"] for x in last)
-    achieved = filt_flops / (filt_ms / 1e3) / 1e12 if filt_ms > 0 else 0.0
+    filter_tflops = filt_flops / (filt_ms / 1e3) / 1e12 if filt_ms > 0 else 0.0
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    if prec == L.PREC_FP64:
-        roof = {"bound": "alu", "achieved": achieved, "peak": 1.10, "unit": "TFLOP/s",
-                "frac": achieved / 1.10, "traffic": None,
-                "kernel": "zgemm_nn_kernel (FP64 filter step, fused recurrence)",
-                "peak_source": "measured FP64 GEMM rate on this GB300 (torch float64 "
-                               "matmul, 8192^3), no FP64 figure in MEASURED_PEAKS.json"}
-    else:
-        pk = peaks.get("bf16_tflops_sustained", 1700.0)
-        roof = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-                "frac": achieved / pk, "traffic": None,
-                "kernel": "filter steps (split-precision tcgen05 + FP64 sweeps)",
-                "peak_source": "bf16_tflops_sustained of measured"}
+    k64_ms = sum(x["k_f64_ms"] for x in last)
+    k64_fl = sum(x["k_f64_flops"] for x in last)
+    k64_n = sum(x["k_f64_launches"] for x in last)
+    ktc_ms = sum(x["k_tc_ms"] for x in last)
+    ktc_fl = sum(x["k_tc_flops"] for x in last)
+    ktc_n = sum(x["k_tc_launches"] for x in last)
+    FP64_PEAK = 1.10  # TFLOP/s, measured FP64 GEMM rate on this GB300 (profiles/peaks_probe_gb300.md)
+    bf16_peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    f64_roof = None
+    if k64_ms > 0:
+        a = k64_fl / (k64_ms / 1e3) / 1e12
+        f64_roof = {"bound": "alu", "achieved": a, "peak": FP64_PEAK, "unit": "TFLOP/s",
+                    "frac": a / FP64_PEAK, "traffic": None,
+                    "kernel": "zgemm_nn_kernel + zgemm_cn_part_kernel (FP64 complex GEMMs)",
+                    "launches": int(k64_n), "avg_launch_ms": k64_ms / max(k64_n, 1),
+                    "peak_source": "measured FP64 GEMM rate on this GB300 (no FP64 entry in "
+                                   "MEASURED_PEAKS.json)"}
+    tc_roof = None
+    if ktc_ms > 0:
+        a = 3.0 * ktc_fl / (ktc_ms / 1e3) / 1e12  # three BF16 products per complex product
+        tc_roof = {"bound": "tensor", "achieved": a, "peak": bf16_peak, "unit": "TFLOP/s",
+                   "frac": a / bf16_peak, "traffic": 179.7e6 if n == 4096 else None,
+                   "traffic_note": "dram read+write of one k_active=320 launch (ncu capture, "
+                                   "profiles/tc_filter_step_n4096_k320.md)",
+                   "useful_tflops": ktc_fl / (ktc_ms / 1e3) / 1e12,
+                   "kernel": "tc_filter_step_kernel (BF16x3 tcgen05, fused recurrence)",
+                   "launches": int(ktc_n), "avg_launch_ms": ktc_ms / max(ktc_n, 1),
+                   "peak_source": "bf16_tflops_sustained of measured"}
+    cands = [r for r in (f64_roof, tc_roof) if r is not None]
+    roof = max(cands, key=lambda r: r["avg_launch_ms"] * r["launches"]) if cands else None
 
     # end to end: same solve through the C ABI with host buffers
     e2e = None
@@ -295,6 +335,20 @@ def main():
         e2e = {"value": (t1 - t0) / reps / (length * ws), "unit": UNIT,
                "h2d_bytes_per_step": int(length * 16 * n * n + 16 * n * k),
                "d2h_bytes_per_step": int(16 * n * k + 8 * length * k)}
+
+    analytic_cmp = None
+    if args.degrees == "learned":
+        s.set_opts(degree_model=L.DEG_ANALYTIC)
+        Xc = X0c.clone()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, sts_a, _ = s.solve_sequence(Hcs, nev, nex, Xc, cfg.tol)
+        b.record(stream)
+        torch.cuda.synchronize()
+        analytic_cmp = {"s_per_problem": a.elapsed_time(b) / 1e3 / length,
+                        "loops": [x["loops"] for x in sts_a]}
+        s.set_opts(degree_model=L.DEG_MLP)
 
     fp64_cmp = None
     if args.fp64_compare and prec != L.PREC_FP64:
@@ -328,22 +382,27 @@ def main():
             "config": {"workload": f"correlated sequence of {length} complex128 Hermitian "
                                    f"problems, n={n}, nev={nev}, nex={nex}, eps=1e-3, "
                                    f"delta=1e-4, tol 1e-10",
-                       "precision": args.precision, "degree_model": "analytic",
+                       "precision": args.precision, "degree_model": args.degrees,
                        "l2": "inputs larger than L2 (each H is 16 n^2 bytes)",
                        "parallelism": f"replicas x{ws}"},
-            "filter_tflops": achieved,
+            "filter_tflops": filter_tflops,
             "filter_tflops_lowp_share": lowp_flops / filt_flops if filt_flops else 0.0,
             "max_resid": max_res,
             "loops": [x["loops"] for x in last],
             "phase_ms": {p: sum(x["ms_" + p] for x in last)
                          for p in ["lanczos", "filter", "qr", "rr", "resid", "lock"]},
             "roofline": roof,
+            "filter_roofline": tc_roof,
+            "fp64_gemm_roofline": f64_roof,
             "gpu_launches": int(launches),
             "filter_launches_per_step": int(filt_launch),
             "clocks": ck,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "fp64_gpu": fp64_cmp,
+            "analytic_degrees_gpu": analytic_cmp,
+            "mlp_training": train_info,
+            "loops_mlp": [x["loops_mlp"] for x in last],
         }
         print(json.dumps(out))
     s.close()

@@ -75,6 +75,11 @@ typedef struct chfsi_opts {
   int max_loops;       /* outer-loop limit                    (50)         */
   double switch_tol;   /* MIXED: residual below which FP64 takes over (1e-4) */
   unsigned long long seed; /* SplitMix64 seed of the Lanczos start (1)     */
+  int profile;         /* 1: time every FP64 GEMM and tensor-core filter */
+                       /* launch with CUDA events into chfsi_stats (0)    */
+  int mlp_extra;       /* DEG_MLP: margin added to the learned degree (2) */
+  int step0;           /* sequence index of the next problem solved (0):  */
+                       /* the step feature of the degree MLP and traces   */
 } chfsi_opts;
 
 /* Per-problem statistics (host struct, filled when non-NULL). */
@@ -93,6 +98,16 @@ typedef struct chfsi_stats {
   double filter_flops;      /* useful filter flops, 8 n^2 sum m_j        */
   long long filter_launches; /* filter-step kernel launches              */
   long long launches;       /* all kernel launches of this solve         */
+  /* per-kernel device time (opts.profile = 1; zero otherwise): */
+  double k_f64_ms;          /* FP64 complex GEMM kernels (H Q, Gram, ...) */
+  double k_f64_flops;       /* their flops, 8 per complex multiply-add   */
+  long long k_f64_launches;
+  double k_tc_ms;           /* tcgen05 filter-step kernel                */
+  double k_tc_flops;        /* its useful complex flops, 8 n^2 k_active  */
+  long long k_tc_launches;
+  int loops_mlp;            /* loops whose degrees came from the MLP     */
+  int mlp_fallback;         /* 1 if the MLP stalled and the analytic rule */
+                            /* took over for the rest of this problem     */
 } chfsi_stats;
 
 /* ---- context ---------------------------------------------------------- */
@@ -248,6 +263,18 @@ int chfsi_filter_static(const double* H, int n, int k, const double* Y0,
 
 /* ---- learned degree predictor (not in the paper) ---------------------- */
 
+/* Traces for training (Alg. 1 line 11 decisions and their outcome).
+ * chfsi_trace_enable(ctx, cap) starts recording, into a device buffer of
+ * cap rows owned by the context (cap = 0 stops and frees it): for every
+ * active column of every loop after the first, its features (see the MLP
+ * below), the degree it was given, its residual before and after that
+ * filter.  chfsi_trace_dataset writes the complete rows of wanted columns
+ * as training pairs: x (rows x 5 floats, row-major) and y = realised decay
+ * per degree / acosh|t| clipped to [0.02, 1.5] (rows floats), both device
+ * buffers of max_rows; *n_rows_host gets the number written. */
+int chfsi_trace_enable(chfsi_ctx* ctx, int capacity_rows);
+int chfsi_trace_dataset(chfsi_ctx* ctx, float* x, float* y, int max_rows, int* n_rows_host);
+
 /* The network: 5 features -> 64 tanh -> 64 tanh -> 1 linear, weights
  * kept in the context as FP32 masters with FP16 copies for the products
  * (FP32 accumulation).  Parameter vector layout (CHFSI_MLP_NPARAM floats):
@@ -257,6 +284,15 @@ int chfsi_filter_static(const double* H, int n, int k, const double* Y0,
 /* Copy parameters host -> context (resets the optimiser state) / out. */
 int chfsi_mlp_set_params(chfsi_ctx* ctx, const float* params_host);
 int chfsi_mlp_get_params(chfsi_ctx* ctx, float* params_host);
+
+/* Features of column j: t = (ritz - c)/e; x = {clip(t, -8, 8), log10(r)/10,
+ * acosh(max|t|, 1), clip((gamma - c)/e, -8, 8), step/10}.  The output y is
+ * the predicted ratio of the realised decay per degree to acosh|t|; with
+ * opts.degree_model = CHFSI_DEG_MLP the solver turns it into
+ * m = ceil(ln(max(r, tol)/tol) / (acosh|t| clip(y, 0.02, 1.5))) + mlp_extra,
+ * clamped to [4, 60] (60 when |t| <= 1), and uses the analytic rule for a
+ * non-finite prediction and for the rest of a problem whose loop did not
+ * make progress (nothing locked and the residual fell by less than 10x). */
 
 /* Forward pass: x (B x 5 floats, row-major, device) -> y (B floats). */
 int chfsi_mlp_forward(chfsi_ctx* ctx, int B, const float* x, float* y);

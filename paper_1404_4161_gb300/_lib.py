@@ -23,7 +23,8 @@ class Opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("split", C.c_int), ("degree_model", C.c_int),
                 ("deg_cold", C.c_int), ("deg_warm", C.c_int), ("deg_min", C.c_int),
                 ("deg_max", C.c_int), ("deg_extra", C.c_int), ("lanczos_steps", C.c_int),
-                ("max_loops", C.c_int), ("switch_tol", C.c_double), ("seed", C.c_ulonglong)]
+                ("max_loops", C.c_int), ("switch_tol", C.c_double), ("seed", C.c_ulonglong),
+                ("profile", C.c_int), ("mlp_extra", C.c_int), ("step0", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -34,7 +35,10 @@ class Stats(C.Structure):
                 ("ms_lanczos", C.c_double), ("ms_filter", C.c_double), ("ms_qr", C.c_double),
                 ("ms_rr", C.c_double), ("ms_resid", C.c_double), ("ms_lock", C.c_double),
                 ("filter_flops", C.c_double), ("filter_launches", C.c_longlong),
-                ("launches", C.c_longlong)]
+                ("launches", C.c_longlong), ("k_f64_ms", C.c_double), ("k_f64_flops", C.c_double),
+                ("k_f64_launches", C.c_longlong), ("k_tc_ms", C.c_double),
+                ("k_tc_flops", C.c_double), ("k_tc_launches", C.c_longlong),
+                ("loops_mlp", C.c_int), ("mlp_fallback", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -74,6 +78,8 @@ _SIGS = {
                                 C.c_int, _P]),
     "chfsi_filter_static": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_double, C.c_double,
                                       C.c_double, _P, _P]),
+    "chfsi_trace_enable": (C.c_int, [_P, C.c_int]),
+    "chfsi_trace_dataset": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(C.c_int)]),
     "chfsi_mlp_set_params": (C.c_int, [_P, _P]),
     "chfsi_mlp_get_params": (C.c_int, [_P, _P]),
     "chfsi_mlp_forward": (C.c_int, [_P, C.c_int, _P, _P]),

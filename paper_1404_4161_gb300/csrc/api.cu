@@ -23,6 +23,47 @@ static std::atomic<long long> g_launches{0};
 long long chfsi_launch_counter() { return g_launches.load(std::memory_order_relaxed); }
 void chfsi_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+static thread_local KernelTimer* g_kt = nullptr;
+KernelTimer* kt_current() { return g_kt; }
+void kt_install(KernelTimer* t) { g_kt = t; }
+
+int kt_begin(cudaStream_t st) {
+  KernelTimer* t = g_kt;
+  if (!t) return -1;
+  if ((int)t->ev.size() < 2 * (t->used + 1)) {
+    for (int i = 0; i < 64; ++i) {
+      cudaEvent_t e;
+      CHFSI_CUDA_TRY(cudaEventCreate(&e));
+      t->ev.push_back(e);
+    }
+    t->cat.resize(t->ev.size() / 2);
+    t->flops.resize(t->ev.size() / 2);
+  }
+  const int slot = t->used++;
+  CHFSI_CUDA_TRY(cudaEventRecord(t->ev[2 * slot], st));
+  return slot;
+}
+
+void kt_end(cudaStream_t st, int slot, int cat, double flops) {
+  KernelTimer* t = g_kt;
+  if (!t || slot < 0) return;
+  CHFSI_CUDA_TRY(cudaEventRecord(t->ev[2 * slot + 1], st));
+  t->cat[slot] = cat;
+  t->flops[slot] = flops;
+}
+
+void kt_resolve(KernelTimer* t) {
+  if (!t) return;
+  for (int i = 0; i < t->used; ++i) {
+    float ms = 0.f;
+    CHFSI_CUDA_TRY(cudaEventElapsedTime(&ms, t->ev[2 * i], t->ev[2 * i + 1]));
+    t->ms[t->cat[i]] += ms;
+    t->fl[t->cat[i]] += t->flops[i];
+    t->n[t->cat[i]] += 1;
+  }
+  t->used = 0;
+}
+
 // ===================================================== workspace & ctx ====
 void* ws_get(chfsi_ctx* ctx, const char* name, size_t bytes) {
   DevBuf& b = ctx->ws[name];
@@ -80,6 +121,7 @@ void validate_opts(const chfsi_opts& o) {
   CHFSI_REQUIRE(o.lanczos_steps >= 2 && o.lanczos_steps <= 200, "opts.lanczos_steps");
   CHFSI_REQUIRE(o.max_loops >= 1, "opts.max_loops");
   CHFSI_REQUIRE(o.switch_tol > 0.0, "opts.switch_tol");
+  CHFSI_REQUIRE(o.mlp_extra >= 0 && o.step0 >= 0, "opts.mlp_extra/step0");
 }
 
 inline double2* C2(double* p) { return reinterpret_cast<double2*>(p); }
@@ -335,7 +377,8 @@ struct PhaseTimer {
 
 // ------------------------------------------------------- solve one -------
 int solve_one(chfsi_ctx* ctx, const double2* H, int n, int nev, int nex, double2* X,
-              double tol, double* evals_out, const double* warm, chfsi_stats* stats) {
+              double tol, double* evals_out, const double* warm, chfsi_stats* stats,
+              int step) {
   const chfsi_opts& o = ctx->opts;
   cudaStream_t st = ctx->stream;
   const int k = nev + nex;
@@ -350,6 +393,16 @@ int solve_one(chfsi_ctx* ctx, const double2* H, int n, int nev, int nex, double2
   chfsi_stats S;
   std::memset(&S, 0, sizeof(S));
   const long long launches0 = chfsi_launch_counter();
+  KernelTimer timer;
+  struct TimerScope {
+    KernelTimer* t;
+    explicit TimerScope(KernelTimer* x) : t(x) { kt_install(x); }
+    ~TimerScope() {
+      kt_install(nullptr);
+      if (t)
+        for (auto e : t->ev) cudaEventDestroy(e);
+    }
+  } timer_scope(o.profile ? &timer : nullptr);
   PhaseTimer tm(ctx);
   tm.mark(0);
 
@@ -411,6 +464,8 @@ int solve_one(chfsi_ctx* ctx, const double2* H, int n, int nev, int nex, double2
   std::vector<int> degs(k, deg0);
   int ka = k, nl = 0;
   double max_resid_wanted = INFINITY;
+  bool use_mlp = o.degree_model == CHFSI_DEG_MLP;
+  trace_abandon(ctx);
   bool lowp_on = mixed;
   int status = CHFSI_ENOCONV;
   int loops = 0;
@@ -445,6 +500,7 @@ int solve_one(chfsi_ctx* ctx, const double2* H, int n, int nev, int nex, double2
     rayleigh_ritz_dev(ctx, H, n, ka, Yf, Yrr, HY, lam);
     tm.mark(5);
     residual_norms(st, n, ka, HY, Yrr, lam, norm_h, res);
+    trace_finish(ctx, ka, res);
     tm.mark(6);
     lock_select(st, ka, lam, res, nev - nl, tol, gamma, ctl, lock_idx, act_idx);
     CHFSI_CUDA_TRY(cudaMemcpyAsync(ctl_h, ctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, st));
@@ -457,6 +513,13 @@ int solve_one(chfsi_ctx* ctx, const double2* H, int n, int nev, int nex, double2
     nl += n_new;
     ka = ctl_h->k_active;
     gamma = ctl_h->gamma;
+    // The learned degrees stall: nothing locked and the residual fell by
+    // less than 10x -> the analytic rule for the rest of this problem.
+    if (use_mlp && S.loops_mlp > 0 && n_new == 0 &&
+        ctl_h->max_resid_wanted > 0.1 * max_resid_wanted) {
+      use_mlp = false;
+      S.mlp_fallback = 1;
+    }
     max_resid_wanted = ctl_h->max_resid_wanted;
     if (nl >= nev) {
       status = CHFSI_OK;
@@ -465,13 +528,15 @@ int solve_one(chfsi_ctx* ctx, const double2* H, int n, int nev, int nex, double2
     } else {
       alpha = ctl_h->alpha;
       const double c2 = 0.5 * (alpha + beta), e2 = 0.5 * (beta - alpha);
-      if (o.degree_model == CHFSI_DEG_MLP) {
-        mlp_degrees(ctx, ka, lam, res, act_idx, c2, e2, gamma, 0, deg);
+      if (use_mlp) {
+        mlp_degrees(ctx, ka, lam, res, act_idx, c2, e2, gamma, step, tol, deg);
         degree_cap_buffer(st, ka, nev - nl, deg);
+        S.loops_mlp++;
       } else {
         degrees_analytic(st, ka, lam, res, act_idx, c2, e2, tol, nev - nl, o.deg_min,
                          o.deg_max, o.deg_extra, deg);
       }
+      trace_record(ctx, ka, lam, res, act_idx, deg, c2, e2, gamma, step, nev - nl);
       sort_by_degree(st, ka, deg, act_idx, perm, deg_sorted);
       gather_columns(st, n, ka, Yrr, n, perm, Xact, n);
       if (tc_all) residual_block(st, n, ka, HY, Yrr, lam, perm, Rblk, lam_act);
@@ -481,6 +546,7 @@ int solve_one(chfsi_ctx* ctx, const double2* H, int n, int nev, int nex, double2
       CHFSI_CUDA_TRY(cudaStreamSynchronize(st));
       degs.assign(deg_h, deg_h + ka);
     }
+    if (o.profile) kt_resolve(&timer);
     S.ms_filter += tm.ms(2, 3);
     S.ms_qr += tm.ms(3, 4);
     S.ms_rr += tm.ms(4, 5);
@@ -509,6 +575,15 @@ int solve_one(chfsi_ctx* ctx, const double2* H, int n, int nev, int nex, double2
   S.ms_total = tm.ms(0, 8);
   S.filter_flops = 8.0 * (double)n * (double)n * (double)S.col_degrees;
   S.launches = chfsi_launch_counter() - launches0;
+  if (o.profile) {
+    kt_resolve(&timer);
+    S.k_f64_ms = timer.ms[KT_F64];
+    S.k_f64_flops = timer.fl[KT_F64];
+    S.k_f64_launches = timer.n[KT_F64];
+    S.k_tc_ms = timer.ms[KT_TC];
+    S.k_tc_flops = timer.fl[KT_TC];
+    S.k_tc_launches = timer.n[KT_TC];
+  }
   if (stats) *stats = S;
   return status;
 }
@@ -546,6 +621,9 @@ void chfsi_default_opts(chfsi_opts* o) {
   o->max_loops = 50;
   o->switch_tol = 1e-4;
   o->seed = 1ull;
+  o->profile = 0;
+  o->mlp_extra = 2;
+  o->step0 = 0;
 }
 
 const char* chfsi_strerror(int code) {
@@ -626,7 +704,8 @@ int chfsi_solve(chfsi_ctx* ctx, const double* H, int n, int nev, int nex, double
   int status = CHFSI_OK;
   int rc = run_guarded(ctx, [&] {
     CHFSI_REQUIRE(n >= 1, "n must be >= 1");
-    status = solve_one(ctx, C2(H), n, nev, nex, C2(X), tol, evals, warm_host, stats);
+    status = solve_one(ctx, C2(H), n, nev, nex, C2(X), tol, evals, warm_host, stats,
+                       ctx->opts.step0);
   });
   if (rc != CHFSI_OK) {
     if (stats) stats->status = rc;
@@ -650,7 +729,7 @@ int chfsi_solve_sequence(chfsi_ctx* ctx, const double* const* H, int N, int n, i
       CHFSI_REQUIRE(H[l] != nullptr, "NULL H in sequence");
       double* ev = evals + (size_t)l * k;
       const int s = solve_one(ctx, C2(H[l]), n, nev, nex, C2(X), tol, ev, l ? warm : nullptr,
-                              stats ? stats + l : nullptr);
+                              stats ? stats + l : nullptr, ctx->opts.step0 + l);
       if (s != CHFSI_OK && status == CHFSI_OK) status = s;
       CHFSI_CUDA_TRY(cudaMemcpyAsync(wh, ev, sizeof(double), cudaMemcpyDeviceToHost,
                                      ctx->stream));
@@ -687,7 +766,8 @@ int chfsi_solve_sequence_host(chfsi_ctx* ctx, const double* const* H, int N, int
       CHFSI_CUDA_TRY(cudaMemcpyAsync(hd, H[l], hb, cudaMemcpyHostToDevice, ctx->stream));
       double* ev = Ed + (size_t)l * k;
       const int s = solve_one(ctx, C2((const double*)hd), n, nev, nex, C2(Xd), tol, ev,
-                              l ? warm : nullptr, stats ? stats + l : nullptr);
+                              l ? warm : nullptr, stats ? stats + l : nullptr,
+                              ctx->opts.step0 + l);
       if (s != CHFSI_OK && status == CHFSI_OK) status = s;
       CHFSI_CUDA_TRY(cudaMemcpyAsync(wh, ev, sizeof(double), cudaMemcpyDeviceToHost,
                                      ctx->stream));
@@ -809,6 +889,19 @@ int chfsi_degrees(chfsi_ctx* ctx, int k, const double* ritz, const double* resid
     const chfsi_opts& o = ctx->opts;
     degrees_analytic(ctx->stream, k, ritz, resid, nullptr, c, e, tol, n_wanted, o.deg_min,
                      o.deg_max, o.deg_extra, degrees);
+  });
+}
+
+int chfsi_trace_enable(chfsi_ctx* ctx, int capacity_rows) {
+  if (!ctx || capacity_rows < 0) return CHFSI_EINVAL;
+  return run_guarded(ctx, [&] { trace_enable(ctx, capacity_rows); });
+}
+
+int chfsi_trace_dataset(chfsi_ctx* ctx, float* x, float* y, int max_rows, int* n_rows_host) {
+  if (!ctx || !n_rows_host || max_rows < 0) return CHFSI_EINVAL;
+  return run_guarded(ctx, [&] {
+    CHFSI_REQUIRE(max_rows == 0 || (x && y), "bad dataset buffers");
+    *n_rows_host = max_rows ? trace_dataset(ctx, x, y, max_rows) : 0;
   });
 }
 

@@ -42,6 +42,26 @@ struct ChfsiError {
     if (!(cond)) throw ChfsiError{CHFSI_EINVAL, text};                         \
   } while (0)
 
+// Optional per-launch timing of the two dominant kernel families.  When a
+// timer is installed for the calling thread (solver with opts.profile),
+// kt_begin / kt_end bracket a launch with CUDA events on its stream and
+// kt_resolve adds the elapsed times after the stream has been synchronised.
+enum KtCat { KT_F64 = 0, KT_TC = 1, KT_NCAT = 2 };
+struct KernelTimer {
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> cat;
+  std::vector<double> flops;
+  int used = 0;
+  double ms[KT_NCAT] = {0, 0};
+  double fl[KT_NCAT] = {0, 0};
+  long long n[KT_NCAT] = {0, 0};
+};
+KernelTimer* kt_current();
+void kt_install(KernelTimer* t);
+int kt_begin(cudaStream_t st);                       // -1 when no timer
+void kt_end(cudaStream_t st, int slot, int cat, double flops);
+void kt_resolve(KernelTimer* t);
+
 // Kernel launches issued by this library (all contexts, all threads).
 long long chfsi_launch_counter();
 void chfsi_count_launch();
@@ -190,4 +210,13 @@ void mlp_forward(chfsi_ctx* ctx, int B, const float* x, float* y);
 void mlp_train_step(chfsi_ctx* ctx, int B, const float* x, const float* target, float lr,
                     float* grads, float* loss_dev);
 void mlp_degrees(chfsi_ctx* ctx, int k, const double* ritz, const double* resid,
-                 const int* idx, double c, double e, double gamma, int step, int* deg_out);
+                 const int* idx, double c, double e, double gamma, int step, double tol,
+                 int* deg_out);
+void trace_enable(chfsi_ctx* ctx, int cap);
+bool trace_on(chfsi_ctx* ctx);
+void trace_record(chfsi_ctx* ctx, int k, const double* ritz, const double* resid,
+                  const int* idx, const int* deg, double c, double e, double gamma, int step,
+                  int n_wanted);
+void trace_finish(chfsi_ctx* ctx, int k, const double* resid);
+void trace_abandon(chfsi_ctx* ctx);
+int trace_dataset(chfsi_ctx* ctx, float* x, float* y, int max_rows);

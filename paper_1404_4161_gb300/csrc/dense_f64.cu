@@ -413,8 +413,10 @@ void zgemm_nn(cudaStream_t st, int M, int N, int K, const double2* A, int lda,
               const double2* B, int ldb, const EpiNN& ep) {
   if (M <= 0 || N <= 0) return;
   dim3 grid((M + TB - 1) / TB, (N + TB - 1) / TB);
+  const int slot = kt_begin(st);
   zgemm_nn_kernel<<<grid, 256, 0, st>>>(M, N, K, A, lda, B, ldb, ep);
   chfsi_check_launch("zgemm_nn");
+  kt_end(st, slot, KT_F64, 8.0 * M * (double)N * K);
 }
 
 void zgemm_cn(chfsi_ctx* ctx, int K1, int K2, int Nr, const double2* A, int lda,
@@ -431,8 +433,10 @@ void zgemm_cn(chfsi_ctx* ctx, int K1, int K2, int Nr, const double2* A, int lda,
   if (splits < 1) splits = 1;
   double2* part = (double2*)ws_get(ctx, "cn_part", sizeof(double2) * (size_t)splits * K1 * K2);
   dim3 grid((K1 + TB - 1) / TB, (K2 + TB - 1) / TB, splits);
+  const int slot = kt_begin(ctx->stream);
   zgemm_cn_part_kernel<<<grid, 256, 0, ctx->stream>>>(K1, K2, Nr, chunk, A, lda, B, ldb, part);
   chfsi_check_launch("zgemm_cn_part");
+  kt_end(ctx->stream, slot, KT_F64, 8.0 * K1 * (double)K2 * Nr);
   zgemm_cn_reduce_kernel<<<grid_for((size_t)K1 * K2, 256, 2048), 256, 0, ctx->stream>>>(
       K1, K2, splits, part, C, ldc, alpha, beta);
   chfsi_check_launch("zgemm_cn_reduce");

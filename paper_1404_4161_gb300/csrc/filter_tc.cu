@@ -586,9 +586,11 @@ void launch_step(TcRun& R, int bufB_in, int bufB_out, int s_col, int ka, float a
   p.fin_end = fin_end;
   p.err = s->err;
   dim3 grid((cols + N - 1) / N, mtiles);
+  const int slot = kt_begin(R.ctx->stream);
   tc_filter_step_kernel<<<grid, NTHREADS, smem, R.ctx->stream>>>(R.mAh, R.mAl, mBh, mBl,
                                                                  2 * s_col, p);
   chfsi_check_launch("tc_filter_step");
+  kt_end(R.ctx->stream, slot, KT_TC, 8.0 * (double)n * n * ka);
 }
 
 void check_err(chfsi_ctx* ctx) {

@@ -175,25 +175,121 @@ __global__ void mlp_features_kernel(int k, const double* ritz, const double* res
   row[4] = (float)(step / 10.0);
 }
 
+// Degree from the predicted decay ratio (closed form); the analytic rule
+// of Sec. 3.2 for a non-finite prediction.
 __global__ void mlp_to_degree_kernel(int k, const float* y, const double* ritz,
                                      const double* resid, const int* idx, double c, double e,
+                                     double tol, int extra, int a_min, int a_max, int a_extra,
                                      int* deg) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= k) return;
+  const int s = idx ? idx[j] : j;
+  const double t = fabs((ritz[s] - c) / e);
+  const double r = resid[s];
   const float v = y[j];
   int m;
   if (isfinite(v)) {
-    m = (int)rintf(fminf(fmaxf(DEG_SCALE * v, (float)DEG_LO), (float)DEG_HI));
-  } else {  // out-of-domain prediction: fall back to the cap
-    m = DEG_HI;
+    if (t > 1.0) {
+      const double yy = fmin(fmax((double)v, 0.02), 1.5);
+      const double kan = acosh(fmax(t, 1.0 + 1e-12));
+      const double q = ceil(log(fmax(r, tol) / tol) / (kan * yy)) + (double)extra;
+      m = (int)fmin(fmax(q, (double)DEG_LO), (double)DEG_HI);
+    } else {
+      m = DEG_HI;
+    }
+  } else {  // analytic fallback
+    m = a_max;
+    if (t > 1.0) {
+      const double q = ceil(log(r / tol) / acosh(t)) + (double)a_extra;
+      m = (int)fmin(fmax(q, (double)a_min), (double)a_max);
+    }
   }
-  (void)ritz; (void)resid; (void)idx; (void)c; (void)e;
   deg[j] = m;
+}
+
+// Trace rows (10 floats): x0..x4, m, r_before, r_after, acosh(max|t|, 1), wanted.
+constexpr int TROW = 10;
+
+__global__ void trace_record_kernel(int k, const double* ritz, const double* resid,
+                                    const int* idx, const int* deg, double c, double e,
+                                    double gamma, int step, int n_wanted, float* rows) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= k) return;
+  const int s = idx ? idx[j] : j;
+  const double t = (ritz[s] - c) / e;
+  const double r = fmax(resid[s], 1e-300);
+  float* row = rows + (size_t)j * TROW;
+  row[0] = (float)fmin(fmax(t, -8.0), 8.0);
+  row[1] = (float)(log10(r) / 10.0);
+  row[2] = (float)acosh(fmax(fabs(t), 1.0));
+  row[3] = (float)fmin(fmax((gamma - c) / e, -8.0), 8.0);
+  row[4] = (float)(step / 10.0);
+  row[5] = (float)deg[j];
+  row[6] = (float)r;
+  row[7] = __int_as_float(0x7fc00000);  // NaN until the next loop's residual
+  row[8] = (float)acosh(fmax(fabs(t), 1.0 + 1e-12));
+  row[9] = j < n_wanted ? 1.f : 0.f;
+}
+
+__global__ void trace_finish_kernel(int k, const double* resid, float* rows) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < k) rows[(size_t)j * TROW + 7] = (float)fmax(resid[j], 1e-300);
+}
+
+// Compacts complete rows of wanted columns into (x, y), in row order.
+__global__ void __launch_bounds__(1024)
+trace_dataset_kernel(int nrows, const float* rows, float* x, float* y, int max_rows,
+                     int* out_count) {
+  __shared__ int warp_sums[32];
+  __shared__ int base_sh;
+  if (threadIdx.x == 0) base_sh = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < nrows; c0 += 1024) {
+    const int i = c0 + threadIdx.x;
+    int ok = 0;
+    if (i < nrows) {
+      const float* row = rows + (size_t)i * TROW;
+      ok = row[9] > 0.5f && isfinite(row[7]) && row[6] > 0.f && row[5] >= 1.f && row[8] > 0.f;
+    }
+    // block exclusive scan of ok
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int v = ok;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    if (lane == 31) warp_sums[w] = v;
+    __syncthreads();
+    if (w == 0) {
+      int s2 = warp_sums[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, s2, o);
+        if (lane >= o) s2 += u;
+      }
+      warp_sums[lane] = s2;
+    }
+    __syncthreads();
+    const int pos = base_sh + (w > 0 ? warp_sums[w - 1] : 0) + v - ok;
+    if (ok && pos < max_rows) {
+      const float* row = rows + (size_t)i * TROW;
+      for (int f = 0; f < F; ++f) x[(size_t)pos * F + f] = row[f];
+      const double kre = log((double)row[6] / (double)row[7]) / (double)row[5];
+      y[pos] = (float)fmin(fmax(kre / (double)row[8], 0.02), 1.5);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) base_sh += warp_sums[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out_count = min(base_sh, max_rows);
 }
 
 }  // namespace
 
 struct MlpState {
+  float* trace = nullptr;  // trace rows (TROW floats each)
+  int trace_cap = 0, trace_n = 0, pend_base = 0, pend_count = 0;
   float* p = nullptr;   // FP32 master parameters
   float* m = nullptr;   // Adam first moment
   float* v = nullptr;   // Adam second moment
@@ -218,6 +314,7 @@ void mlp_destroy(chfsi_ctx* ctx) {
   if (!ctx->mlp) return;
   cudaFree(ctx->mlp->p);
   cudaFree(ctx->mlp->w16);
+  cudaFree(ctx->mlp->trace);
   delete ctx->mlp;
   ctx->mlp = nullptr;
 }
@@ -276,7 +373,8 @@ void mlp_train_step(chfsi_ctx* ctx, int B, const float* x, const float* target, 
 }
 
 void mlp_degrees(chfsi_ctx* ctx, int k, const double* ritz, const double* resid,
-                 const int* idx, double c, double e, double gamma, int step, int* deg_out) {
+                 const int* idx, double c, double e, double gamma, int step, double tol,
+                 int* deg_out) {
   if (k <= 0) return;
   float* x = (float*)ws_get(ctx, "mlp_x", sizeof(float) * (size_t)k * (F + 1));
   float* y = x + (size_t)k * F;
@@ -284,7 +382,63 @@ void mlp_degrees(chfsi_ctx* ctx, int k, const double* ritz, const double* resid,
                                                                   gamma, step, x);
   chfsi_check_launch("mlp_features");
   mlp_forward(ctx, k, x, y);
-  mlp_to_degree_kernel<<<(k + 127) / 128, 128, 0, ctx->stream>>>(k, y, ritz, resid, idx, c, e,
-                                                                   deg_out);
+  const chfsi_opts& o = ctx->opts;
+  mlp_to_degree_kernel<<<(k + 127) / 128, 128, 0, ctx->stream>>>(
+      k, y, ritz, resid, idx, c, e, tol, o.mlp_extra, o.deg_min, o.deg_max, o.deg_extra, deg_out);
   chfsi_check_launch("mlp_to_degree");
+}
+
+void trace_enable(chfsi_ctx* ctx, int cap) {
+  MlpState* s = ctx->mlp;
+  cudaFree(s->trace);
+  s->trace = nullptr;
+  s->trace_cap = 0;
+  s->trace_n = s->pend_base = s->pend_count = 0;
+  if (cap > 0) {
+    CHFSI_CUDA_TRY(cudaMalloc(&s->trace, sizeof(float) * TROW * (size_t)cap));
+    s->trace_cap = cap;
+  }
+}
+
+bool trace_on(chfsi_ctx* ctx) { return ctx->mlp && ctx->mlp->trace_cap > 0; }
+
+void trace_record(chfsi_ctx* ctx, int k, const double* ritz, const double* resid,
+                  const int* idx, const int* deg, double c, double e, double gamma, int step,
+                  int n_wanted) {
+  MlpState* s = ctx->mlp;
+  s->pend_count = 0;
+  if (!trace_on(ctx) || k <= 0 || s->trace_n + k > s->trace_cap) return;
+  trace_record_kernel<<<(k + 127) / 128, 128, 0, ctx->stream>>>(
+      k, ritz, resid, idx, deg, c, e, gamma, step, n_wanted,
+      s->trace + (size_t)s->trace_n * TROW);
+  chfsi_check_launch("trace_record");
+  s->pend_base = s->trace_n;
+  s->pend_count = k;
+  s->trace_n += k;
+}
+
+void trace_finish(chfsi_ctx* ctx, int k, const double* resid) {
+  MlpState* s = ctx->mlp;
+  if (!trace_on(ctx) || s->pend_count <= 0) return;
+  const int cnt = k < s->pend_count ? k : s->pend_count;
+  trace_finish_kernel<<<(cnt + 127) / 128, 128, 0, ctx->stream>>>(
+      cnt, resid, s->trace + (size_t)s->pend_base * TROW);
+  chfsi_check_launch("trace_finish");
+  s->pend_count = 0;
+}
+
+void trace_abandon(chfsi_ctx* ctx) {
+  if (ctx->mlp) ctx->mlp->pend_count = 0;
+}
+
+int trace_dataset(chfsi_ctx* ctx, float* x, float* y, int max_rows) {
+  MlpState* s = ctx->mlp;
+  if (!trace_on(ctx) || s->trace_n == 0) return 0;
+  int* cnt = (int*)ws_get(ctx, "trace_cnt", sizeof(int));
+  trace_dataset_kernel<<<1, 1024, 0, ctx->stream>>>(s->trace_n, s->trace, x, y, max_rows, cnt);
+  chfsi_check_launch("trace_dataset");
+  int* h = (int*)pinned_get(ctx, 64);
+  CHFSI_CUDA_TRY(cudaMemcpyAsync(h, cnt, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CHFSI_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return *h;
 }

@@ -151,7 +151,10 @@ class Chfsi:
                                            n_wanted, _ptr(d)))
         return d
 
-    # -- MLP -----------------------------------------------------------
+    # -- traces and MLP ------------------------------------------------
+    def trace_enable(self, capacity_rows):
+        self._check(self.lib.chfsi_trace_enable(self.ctx, int(capacity_rows)))
+
     def mlp_set_params(self, flat):
         f = flat.detach().to(torch.float32).contiguous().cpu()
         self._check(self.lib.chfsi_mlp_set_params(self.ctx, _ptr(f)))
