@@ -185,6 +185,25 @@ int chfsi_filter(chfsi_ctx* ctx, const double* H, int n, int k, const double* Y0
                  const int* degrees_host, double lam1, double c, double e,
                  double* Y, int precision);
 
+/* One problem of chfsi_filter_batched (same meaning as chfsi_filter's
+ * arguments; every pointer is a device pointer except degrees_host). */
+typedef struct chfsi_filter_item {
+  const double* H;          /* complex n x n Hermitian                     */
+  int n, k;
+  const double* Y0;         /* complex n x k, ascending-degree columns      */
+  const int* degrees_host;  /* k ints >= 1, ascending                       */
+  double lam1, c, e;
+  double* Y;                /* complex n x k output (not aliasing Y0)       */
+} chfsi_filter_item;
+
+/* Alg. 2 for P independent problems of any sizes in one persistent,
+ * cooperative tensor-core launch (split precision as CHFSI_PREC_MIXED):
+ * one CTA per SM walks a list of (step, problem, tile) work items; a step
+ * of a problem starts when that problem's previous step is complete
+ * (bounded device waits; CHFSI_ETIMEOUT if one gives up).  Results equal
+ * chfsi_filter(..., CHFSI_PREC_MIXED) problem by problem. */
+int chfsi_filter_batched(chfsi_ctx* ctx, int P, const chfsi_filter_item* items);
+
 /* Alg. 2 in refinement form (not in the paper): for Ritz pairs (Y, ritz)
  * of H and R = H Y - Y diag(ritz), returns Y_m = p_m(H) Y exactly as
  * chfsi_filter would, computed as Y psi_m(ritz) + D_m: psi_m is the

@@ -44,6 +44,12 @@ class Stats(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class FilterItem(C.Structure):
+    _fields_ = [("H", C.c_void_p), ("n", C.c_int), ("k", C.c_int), ("Y0", C.c_void_p),
+                ("degrees_host", C.POINTER(C.c_int)), ("lam1", C.c_double), ("c", C.c_double),
+                ("e", C.c_double), ("Y", C.c_void_p)]
+
+
 class ChfsiError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"chfsi error {code}: {msg}")
@@ -69,6 +75,7 @@ _SIGS = {
     "chfsi_lanczos": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_ulonglong, _P]),
     "chfsi_filter": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, C.c_double, C.c_double,
                                C.c_double, _P, C.c_int]),
+    "chfsi_filter_batched": (C.c_int, [_P, C.c_int, _P]),
     "chfsi_filter_refine": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, _P, _P, C.c_double,
                                       C.c_double, C.c_double, _P]),
     "chfsi_orthonormalize": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_int, _P]),

@@ -689,6 +689,7 @@ void chfsi_free(chfsi_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
   tc_filter_release(ctx);
+  tc_filter_batched_release(ctx);
   mlp_destroy(ctx);
   ws_free_all(ctx);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
@@ -821,6 +822,43 @@ int chfsi_filter(chfsi_ctx* ctx, const double* H, int n, int k, const double* Y0
       CHFSI_REQUIRE(precision == CHFSI_PREC_FP64, "bad precision");
       filter_f64(ctx, C2(H), n, k, C2(Y0), degrees_host, lam1, c, e, C2(Y));
     }
+  });
+}
+
+int chfsi_filter_batched(chfsi_ctx* ctx, int P, const chfsi_filter_item* items) {
+  if (!ctx) return CHFSI_EINVAL;
+  return run_guarded(ctx, [&] {
+    CHFSI_REQUIRE(P >= 0 && (P == 0 || items), "bad batch");
+    if (!tc_filter_supported(ctx))
+      throw ChfsiError{CHFSI_ENOTSUP, "split-precision filter needs an sm_103 device"};
+    std::vector<TcBatchItem> v;
+    for (int p = 0; p < P; ++p) {
+      const chfsi_filter_item& it = items[p];
+      CHFSI_REQUIRE(it.n >= 1 && it.k >= 0 && it.k <= it.n, "bad batched filter sizes");
+      if (it.k == 0) continue;
+      CHFSI_REQUIRE(it.H && it.Y0 && it.Y && it.degrees_host && it.Y0 != it.Y,
+                    "bad batched filter buffers");
+      CHFSI_REQUIRE(it.e > 0.0 && it.lam1 != it.c, "bad filter interval");
+      for (int j = 0; j < it.k; ++j) {
+        CHFSI_REQUIRE(it.degrees_host[j] >= 1, "degrees must be >= 1");
+        CHFSI_REQUIRE(j == 0 || it.degrees_host[j] >= it.degrees_host[j - 1],
+                      "degrees must be ascending");
+      }
+      TcBatchItem b;
+      b.H = C2(it.H);
+      b.n = it.n;
+      b.k = it.k;
+      b.src = C2(it.Y0);
+      b.R = nullptr;
+      b.fR = nullptr;
+      b.deg = it.degrees_host;
+      b.lam1 = it.lam1;
+      b.c = it.c;
+      b.e = it.e;
+      b.out = C2(it.Y);
+      v.push_back(b);
+    }
+    tc_filter_batched_run(ctx, (int)v.size(), v.data());
   });
 }
 

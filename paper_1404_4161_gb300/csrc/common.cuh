@@ -197,6 +197,25 @@ void tc_filter_run_defect(chfsi_ctx* ctx, const double2* H, int n, int k, const 
                           const double2* Rres, const double* lam, const int* deg_host,
                           const int* deg_dev, double lam1, double c, double e, double2* Yout);
 void tc_filter_release(chfsi_ctx* ctx);
+// Launchers of the operand-preparation kernels (filter_tc.cu).
+void tc_repack_h(cudaStream_t st, int n, int P, const double2* H, void* Ah, void* Al);
+void tc_split_block(cudaStream_t st, int n, int k, int P, const double2* src, double scale,
+                    float2* master, void* bh, void* bl, double2* out, int fin_end);
+// One problem of a batched filter launch (filter_batched.cu).  Plain form:
+// src = Y0, R = fR = null.  Refinement form: R = residual block, fR =
+// forcing table ((m_k + 1) x k, row i for step i); out receives D.
+struct TcBatchItem {
+  const double2* H;
+  int n, k;
+  const double2* src;
+  const double2* R;
+  const double* fR;
+  const int* deg;  // host, ascending
+  double lam1, c, e;
+  double2* out;
+};
+void tc_filter_batched_run(chfsi_ctx* ctx, int P, const TcBatchItem* items);
+void tc_filter_batched_release(chfsi_ctx* ctx);
 // R[:, j] = HY[:, perm[j]] - lam[perm[j]] Y[:, perm[j]], lam_out[j] = lam[perm[j]].
 void residual_block(cudaStream_t st, int n, int k, const double2* HY, const double2* Y,
                     const double* lam, const int* perm, double2* R, double* lam_out);

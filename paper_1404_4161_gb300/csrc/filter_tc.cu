@@ -37,137 +37,15 @@
 // D is of the size of the residual, so computing it in split precision
 // leaves an error of (split precision) x (residual) instead of the split
 // precision itself; Y psi(Lambda) is formed in FP64.
-#include <cuda.h>
-#include <cuda_bf16.h>
-#include <cudaTypedefs.h>
-
 #include <algorithm>
 #include <cmath>
 #include <vector>
 
-#include "common.cuh"
+#include "tc_ptx.cuh"
 
 namespace {
 
-constexpr int BM = 128;        // tile rows (UMMA M)
-constexpr int BK = 64;         // K block (one 128-byte swizzle row of bf16)
-constexpr int NTHREADS = 256;
-constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s per wait
-
-// ------------------------------------------------------------ PTX -------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ unsigned long long globaltimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait.  Returns false (and raises the CTA abort flag and the
-// global error word) when the phase did not complete in time, or when
-// another role of this CTA has already aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_sh,
-                                          int* err, int code) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = globaltimer();
-  while (!mbar_try_wait(bar, parity)) {
-    if (*abort_sh) return false;
-    if (globaltimer() - t0 > WAIT_NS) {
-      *abort_sh = 1;
-      atomicExch(err, code);
-      return false;
-    }
-  }
-  return true;
-}
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
-      "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                   smem_u32(dst_smem)),
-               "r"(ncols));
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                          uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
-}
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Shared-memory matrix descriptor, K-major operand with 128-byte swizzle:
-// start address >> 4 (bits 0-13), leading-dimension offset 16 B (unused
-// for this layout), stride offset 1024 B between 8-row groups (bits
-// 32-45), descriptor version 1 (bit 46), swizzle mode 2 = 128 B (61-63).
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
-         ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16
-// (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at
-// bits 24-28.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-  hi = __float2bfloat16_rn(x);
-  lo = __float2bfloat16_rn(x - __bfloat162float(hi));
-}
+using namespace tcx;
 
 // ------------------------------------------------------------ kernel ----
 struct StepParams {
@@ -420,37 +298,6 @@ __global__ void scale_rows_kernel(int rows, int k, const double* __restrict__ ps
 }
 
 // ------------------------------------------------------------ host ------
-PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    cudaDriverEntryPointQueryResult q;
-    void* p = nullptr;
-    CHFSI_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                                    cudaEnableDefault, &q));
-    if (q != cudaDriverEntryPointSuccess || !p)
-      throw ChfsiError{CHFSI_ENOTSUP, "cuTensorMapEncodeTiled unavailable"};
-    fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-  }
-  return fn;
-}
-
-// 2-D bf16 map over a (rows x cols) array with row pitch P elements; box
-// (64 x box_rows), 128-byte swizzle, zero fill outside the extent.
-CUtensorMap make_map(const void* base, int cols, int rows, int P, int box_rows) {
-  CUtensorMap m;
-  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)P * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
-  const cuuint32_t estr[2] = {1, 1};
-  CUresult r = get_encode()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base),
-                            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS)
-    throw ChfsiError{CHFSI_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")"};
-  return m;
-}
-
 // Tile N (real columns, multiple of 16, <= 256) for `cols` active real
 // columns and `mtiles` row tiles: fewest waves over the SMs, then the
 // smallest per-CTA width (a fixed per-tile cost of 32 columns is added).
@@ -526,6 +373,19 @@ static void tc_reserve(chfsi_ctx* ctx, int n, int k) {
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     s->attr_set = true;
   }
+}
+
+void tc_repack_h(cudaStream_t st, int n, int P, const double2* H, void* Ah, void* Al) {
+  dim3 grid((2 * n + 255) / 256, n);
+  repack_h_kernel<<<grid, 256, 0, st>>>(n, P, H, (__nv_bfloat16*)Ah, (__nv_bfloat16*)Al);
+  chfsi_check_launch("repack_h");
+}
+
+void tc_split_block(cudaStream_t st, int n, int k, int P, const double2* src, double scale,
+                    float2* master, void* bh, void* bl, double2* out, int fin_end) {
+  split_block_kernel<<<dim3((n + 255) / 256, k), 256, 0, st>>>(
+      n, k, P, src, scale, master, (__nv_bfloat16*)bh, (__nv_bfloat16*)bl, out, fin_end);
+  chfsi_check_launch("split_block");
 }
 
 void tc_filter_prepare(chfsi_ctx* ctx, const double2* H, int n) {

@@ -113,6 +113,21 @@ class Chfsi:
                                           precision))
         return out
 
+    def filter_batched(self, jobs):
+        """jobs: list of (Hc, Y0c, degrees, lam1, c, e); one launch for all."""
+        items = (L.FilterItem * max(len(jobs), 1))()
+        outs, keep = [], []
+        for i, (Hc, Y0c, degrees, lam1, c, e) in enumerate(jobs):
+            k, n = Y0c.shape
+            out = torch.empty_like(Y0c)
+            d = (C.c_int * max(k, 1))(*[int(x) for x in degrees])
+            keep.append(d)
+            items[i] = L.FilterItem(Hc.data_ptr(), n, k, Y0c.data_ptr(), d, lam1, c, e,
+                                    out.data_ptr())
+            outs.append(out)
+        self._check(self.lib.chfsi_filter_batched(self.ctx, len(jobs), C.cast(items, C.c_void_p)))
+        return outs
+
     def filter_refine(self, Hc, Yc, Rc, ritz, degrees, lam1, c, e):
         k, n = Yc.shape
         out = torch.empty_like(Yc)
