@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--degrees", choices=["learned", "analytic"], default="learned")
+    ap.add_argument("--batched-scale", type=float, default=0.25,
+                    help="n range of the 64-problem batched measurement, as a fraction of "
+                         "[1500, 6000] (0 skips it)")
     ap.add_argument("--train-length", type=int, default=4,
                     help="problems in the (separate) training sequence of the degree MLP")
     return ap.parse_args()
@@ -182,6 +185,55 @@ def cpu_baseline_sample(Hs_host, nev, nex, tol, X0, length):
     return {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "sample": f"problems 1 (random start) and 2 (warm start), value = (t1 + "
                       f"{length - 1} t2)/{length}; t1 {t1 - t0:.2f} s, t2 {t2 - t1:.2f} s"}
+
+
+def measure_batched(scale, dev, stream, prec):
+    """64 independent sequences (k-point style): n uniform in scale x [1500,
+    6000], nev = n/16, nex = nev/4, 2 steps each; lockstep batched solve
+    (one batched filter launch per loop) against the same problems solved
+    one at a time."""
+    import torch
+    from paper_1404_4161_gb300 import _lib as L
+    from paper_1404_4161_gb300.solver import Chfsi, colmajor
+    from workloads.synthetic import CONFIGS, config_sequence, random_block
+    cfg = CONFIGS[4]
+    rng = np.random.Generator(np.random.PCG64(14044161 + 4000))
+    lo, hi = int(1500 * scale), int(6000 * scale)
+    seqs, steps = [], 2
+    for p in range(64):
+        n = int(rng.integers(lo, hi + 1))
+        nev = max(1, n // 16)
+        nex = max(1, nev // 4)
+        Hs, _ = config_sequence(cfg, 14044161 + 4100 + p, length=steps, n=n)
+        X0 = random_block(n, nev + nex, 14044161 + 4300 + p)
+        seqs.append(([colmajor(torch.from_numpy(h).to(dev)) for h in Hs], nev, nex,
+                     colmajor(torch.from_numpy(X0).to(dev))))
+    s = Chfsi(precision=prec if prec != L.PREC_FP64 else L.PREC_TC, profile=1)
+    work = [(H, nev, nex, X.clone()) for H, nev, nex, X in seqs]
+    s.solve_batched(work, 1e-10)  # warm-up
+    work = [(H, nev, nex, X.clone()) for H, nev, nex, X in seqs]
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    evs, stats, rc = s.solve_batched(work, 1e-10)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_batch = a.elapsed_time(b) / 1e3
+    filt_ms = sum(st[0]["k_tc_ms"] for st in stats)
+    filt_fl = sum(st[0]["k_tc_flops"] for st in stats)
+    a.record(stream)
+    for H, nev, nex, X in seqs:
+        s.solve_sequence(H, nev, nex, X.clone(), 1e-10)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_seq = a.elapsed_time(b) / 1e3
+    s.close()
+    return {"problems": 64 * steps, "n_range": [lo, hi], "steps": steps, "rc": rc,
+            "s_per_problem_batched": t_batch / (64 * steps),
+            "s_per_problem_one_at_a_time": t_seq / (64 * steps),
+            "batched_filter_useful_tflops": filt_fl / (filt_ms / 1e3) / 1e12 if filt_ms else None,
+            "batched_filter_executed_tflops": 3 * filt_fl / (filt_ms / 1e3) / 1e12 if filt_ms else None,
+            "max_loops": max(st["loops"] for row in stats for st in row)}
 
 
 def main():
@@ -367,6 +419,10 @@ def main():
         fp64_cmp = {"s_per_problem": a.elapsed_time(b) / 1e3 / m, "problems": m}
         s64.close()
 
+    batched = None
+    if args.batched_scale > 0:
+        batched = measure_batched(args.batched_scale, dev, stream, prec)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and length >= 2:
         Hh2 = [Hcs[0].t().cpu().numpy(), Hcs[1].t().cpu().numpy()]
@@ -402,6 +458,7 @@ def main():
             "fp64_gpu": fp64_cmp,
             "analytic_degrees_gpu": analytic_cmp,
             "mlp_training": train_info,
+            "batched": batched,
             "loops_mlp": [x["loops_mlp"] for x in last],
         }
         print(json.dumps(out))

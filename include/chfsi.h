@@ -166,6 +166,27 @@ int chfsi_solve_sequence_host(chfsi_ctx* ctx, const double* const* H_host, int N
                               int n, int nev, int nex, double* X_host, double tol,
                               double* evals_host, chfsi_stats* stats_host);
 
+/* One independent sequence of chfsi_solve_batched. */
+typedef struct chfsi_problem {
+  const double* const* H_host; /* host array of `steps` device pointers to */
+                               /* complex n x n Hermitian matrices          */
+  int n, nev, nex;
+  double* X;                   /* device, complex n x (nev+nex): in X0,     */
+                               /* out the Ritz block of the last step        */
+  double* evals;               /* device, steps x (nev+nex) doubles          */
+} chfsi_problem;
+
+/* Many independent sequences (k-point style) solved in lockstep: at each
+ * step l, problem p starts from its step l-1 Ritz block (random start at
+ * l = 0), and every outer loop filters all unconverged problems in ONE
+ * batched persistent tensor-core launch (opts.precision CHFSI_PREC_TC or
+ * CHFSI_PREC_MIXED; FP64 filters run per problem), followed by each
+ * problem's QR, Rayleigh-Ritz, residuals, locking and degrees.
+ *  stats_host  NULL or steps * P structs, entry l * P + p; with
+ *  opts.profile the batch's kernel times are reported in entry l * P. */
+int chfsi_solve_batched(chfsi_ctx* ctx, int P, const chfsi_problem* probs, int steps,
+                        double tol, chfsi_stats* stats_host);
+
 /* ---- the steps of the hot path, one entry point each ------------------ */
 
 /* Alg. 1 line 3: s-step Lanczos with full reorthogonalisation from the

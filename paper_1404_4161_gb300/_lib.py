@@ -50,6 +50,11 @@ class FilterItem(C.Structure):
                 ("e", C.c_double), ("Y", C.c_void_p)]
 
 
+class Problem(C.Structure):
+    _fields_ = [("H_host", C.c_void_p), ("n", C.c_int), ("nev", C.c_int), ("nex", C.c_int),
+                ("X", C.c_void_p), ("evals", C.c_void_p)]
+
+
 class ChfsiError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"chfsi error {code}: {msg}")
@@ -72,6 +77,7 @@ _SIGS = {
                                        C.c_double, _P, _P]),
     "chfsi_solve_sequence_host": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, _P,
                                             C.c_double, _P, _P]),
+    "chfsi_solve_batched": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_double, _P]),
     "chfsi_lanczos": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_ulonglong, _P]),
     "chfsi_filter": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, C.c_double, C.c_double,
                                C.c_double, _P, C.c_int]),

@@ -362,147 +362,212 @@ void rayleigh_ritz_dev(chfsi_ctx* ctx, const double2* H, int n, int k, const dou
   }
 }
 
-// ---------------------------------------------------------- timing -------
-struct PhaseTimer {
-  chfsi_ctx* ctx;
-  int cur = 0;
-  explicit PhaseTimer(chfsi_ctx* c) : ctx(c) {}
-  void mark(int i) { CHFSI_CUDA_TRY(cudaEventRecord(ctx->ev[i], ctx->stream)); }
+// ------------------------------------------------- one problem's state --
+// Alg. 1 for one problem, split into phases so that several problems can
+// share a batched filter launch: init (checks, Lanczos, interval), filter,
+// post (QR, Rayleigh-Ritz, residuals, locking, degrees), finish (output).
+struct Problem {
+  chfsi_ctx* ctx = nullptr;
+  const chfsi_opts* o = nullptr;
+  cudaStream_t st = nullptr;
+  std::string pre;  // workspace-name prefix (one per concurrent problem)
+  const double2* H = nullptr;
+  int n = 0, nev = 0, nex = 0, k = 0, step = 0;
+  double2* X = nullptr;
+  double* evals_out = nullptr;
+  double tol = 0.0;
+  chfsi_stats* stats_out = nullptr;
+  bool mixed = false, tc_all = false;
+  double2 *Xact = nullptr, *Yf = nullptr, *Yrr = nullptr, *HY = nullptr, *Lk = nullptr,
+          *Rblk = nullptr;
+  double *lam = nullptr, *res = nullptr, *lamL = nullptr, *resL = nullptr, *lam_act = nullptr,
+         *bnd = nullptr;
+  int *lock_idx = nullptr, *act_idx = nullptr, *deg = nullptr, *perm = nullptr,
+      *deg_sorted = nullptr;
+  LoopCtl* ctl = nullptr;
+  double beta = 0, norm_h = 0, alpha = 0, gamma = 0, max_resid_wanted = INFINITY;
+  int ka = 0, nl = 0, loops = 0, status = CHFSI_ENOCONV;
+  bool use_mlp = false, lowp_on = false, done = false;
+  std::vector<int> degs;
+  chfsi_stats S;
+  long long launches0 = 0, fl0 = 0;
+  long long sdeg = 0;
+  cudaEvent_t ev[9] = {};
+  double* psi = nullptr;  // refinement tables of the current loop
+  double* fR = nullptr;
+
+  void* ws(const char* name, size_t bytes) { return ws_get(ctx, (pre + name).c_str(), bytes); }
+  void mark(int i) { CHFSI_CUDA_TRY(cudaEventRecord(ev[i], st)); }
   double ms(int a, int b) {
     float t = 0.f;
-    CHFSI_CUDA_TRY(cudaEventElapsedTime(&t, ctx->ev[a], ctx->ev[b]));
+    CHFSI_CUDA_TRY(cudaEventElapsedTime(&t, ev[a], ev[b]));
     return (double)t;
   }
-};
-
-// ------------------------------------------------------- solve one -------
-int solve_one(chfsi_ctx* ctx, const double2* H, int n, int nev, int nex, double2* X,
-              double tol, double* evals_out, const double* warm, chfsi_stats* stats,
-              int step) {
-  const chfsi_opts& o = ctx->opts;
-  cudaStream_t st = ctx->stream;
-  const int k = nev + nex;
-  CHFSI_REQUIRE(H && X && evals_out, "NULL buffer");
-  CHFSI_REQUIRE(nev >= 1 && nex >= 1 && k <= n, "need 1 <= nev, 1 <= nex, nev + nex <= n");
-  CHFSI_REQUIRE(tol > 0.0, "tol must be > 0");
-  const bool mixed = o.precision == CHFSI_PREC_MIXED;
-  const bool tc_all = o.precision == CHFSI_PREC_TC;
-  if ((mixed || tc_all) && !tc_filter_supported(ctx))
-    throw ChfsiError{CHFSI_ENOTSUP, "split-precision filter needs an sm_103 device"};
-
-  chfsi_stats S;
-  std::memset(&S, 0, sizeof(S));
-  const long long launches0 = chfsi_launch_counter();
-  KernelTimer timer;
-  struct TimerScope {
-    KernelTimer* t;
-    explicit TimerScope(KernelTimer* x) : t(x) { kt_install(x); }
-    ~TimerScope() {
-      kt_install(nullptr);
-      if (t)
-        for (auto e : t->ev) cudaEventDestroy(e);
-    }
-  } timer_scope(o.profile ? &timer : nullptr);
-  PhaseTimer tm(ctx);
-  tm.mark(0);
-
-  const size_t blk = sizeof(double2) * (size_t)n * k;
-  double2* Xact = (double2*)ws_get(ctx, "s_Xact", blk);
-  double2* Yf = (double2*)ws_get(ctx, "s_Yf", blk);
-  double2* Yrr = (double2*)ws_get(ctx, "s_Yrr", blk);
-  double2* HY = (double2*)ws_get(ctx, "s_HY", blk);
-  double2* Lk = (double2*)ws_get(ctx, "s_Lk", sizeof(double2) * (size_t)n * nev);
-  double* lam = (double*)ws_get(ctx, "s_lam", sizeof(double) * k);
-  double* res = (double*)ws_get(ctx, "s_res", sizeof(double) * k);
-  double* lamL = (double*)ws_get(ctx, "s_lamL", sizeof(double) * nev);
-  double* resL = (double*)ws_get(ctx, "s_resL", sizeof(double) * nev);
-  double2* Rblk = tc_all ? (double2*)ws_get(ctx, "s_Rblk", blk) : nullptr;
-  double* lam_act = (double*)ws_get(ctx, "s_lamact", sizeof(double) * k);
-  int* iws = (int*)ws_get(ctx, "s_int", sizeof(int) * 5 * (size_t)k);
-  int* lock_idx = iws;
-  int* act_idx = iws + k;
-  int* deg = iws + 2 * k;
-  int* perm = iws + 3 * k;
-  int* deg_sorted = iws + 4 * k;
-  double* bnd = (double*)ws_get(ctx, "s_bnd", sizeof(double) * 4);
-  LoopCtl* ctl = (LoopCtl*)ws_get(ctx, "s_ctl", sizeof(LoopCtl));
-  char* hp = (char*)pinned_get(ctx, 1024 + sizeof(int) * (size_t)k + sizeof(double) * k);
-  LoopCtl* ctl_h = (LoopCtl*)(hp + 256);
-  double* bnd_h = (double*)(hp + 512);
-  int* deg_h = (int*)(hp + 1024);
-
-  if (any_nonfinite(ctx, (size_t)2 * n * k, (const double*)X))
-    throw ChfsiError{CHFSI_ENAN, "NaN/Inf in the starting block"};
-  if (any_nonfinite(ctx, (size_t)2 * n * n, (const double*)H))
-    throw ChfsiError{CHFSI_ENAN, "NaN/Inf in H"};
-  // Alg. 1 line 3: bounds of the spectrum.
-  lanczos_dev(ctx, H, n, o.lanczos_steps, o.seed, bnd);
-  CHFSI_CUDA_TRY(cudaMemcpyAsync(bnd_h, bnd, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
-  tm.mark(1);
-  CHFSI_CUDA_TRY(cudaStreamSynchronize(st));
-  S.ms_lanczos = tm.ms(0, 1);
-  const double beta = bnd_h[0];
-  const double norm_h = bnd_h[3];
-  if (!std::isfinite(beta) || !std::isfinite(norm_h) || norm_h <= 0.0)
-    throw ChfsiError{CHFSI_ENAN, "Lanczos bounds are not finite"};
-  S.beta = beta;
-  S.norm_h = norm_h;
-  double alpha, gamma;
-  int deg0;
-  if (warm) {
-    gamma = warm[0];
-    alpha = warm[1];
-    deg0 = o.deg_warm;
-  } else {
-    gamma = bnd_h[1];
-    alpha = gamma + (beta - gamma) * (double)k / (double)n;
-    deg0 = o.deg_cold;
+  ~Problem() {
+    for (auto e : ev)
+      if (e) cudaEventDestroy(e);
   }
-  CHFSI_REQUIRE(alpha < beta, "filter interval is empty (alpha >= beta)");
 
-  copy_columns(st, n, k, X, n, Xact, n);
-  std::vector<int> degs(k, deg0);
-  int ka = k, nl = 0;
-  double max_resid_wanted = INFINITY;
-  bool use_mlp = o.degree_model == CHFSI_DEG_MLP;
-  trace_abandon(ctx);
-  bool lowp_on = mixed;
-  int status = CHFSI_ENOCONV;
-  int loops = 0;
-  while (loops < o.max_loops) {
-    ++loops;
-    const double c = 0.5 * (alpha + beta), e = 0.5 * (beta - alpha);
-    if (lowp_on && !(max_resid_wanted > o.switch_tol)) lowp_on = false;
-    long long sdeg = 0;
-    for (int j = 0; j < ka; ++j) sdeg += degs[j];
-    tm.mark(2);
-    const long long fl0 = chfsi_launch_counter();
-    if (tc_all) {
-      if (loops == 1)
-        tc_filter_run(ctx, H, n, ka, Xact, degs.data(), gamma, c, e, Yf);
-      else
-        tc_filter_run_defect(ctx, H, n, ka, Xact, Rblk, lam_act, degs.data(), deg_sorted, gamma,
-                             c, e, Yf);
-      S.loops_lowp++;
-      S.col_degrees_lowp += sdeg;
-    } else if (lowp_on) {
-      tc_filter_run(ctx, H, n, ka, Xact, degs.data(), gamma, c, e, Yf);
-      S.loops_lowp++;
-      S.col_degrees_lowp += sdeg;
+  void init(chfsi_ctx* c, const std::string& prefix, const double2* H_, int n_, int nev_,
+            int nex_, double2* X_, double tol_, double* evals_, const double* warm,
+            chfsi_stats* stats_, int step_) {
+    ctx = c;
+    o = &ctx->opts;
+    st = ctx->stream;
+    pre = prefix;
+    H = H_;
+    n = n_;
+    nev = nev_;
+    nex = nex_;
+    k = nev + nex;
+    X = X_;
+    tol = tol_;
+    evals_out = evals_;
+    stats_out = stats_;
+    step = step_;
+    CHFSI_REQUIRE(H && X && evals_out, "NULL buffer");
+    CHFSI_REQUIRE(nev >= 1 && nex >= 1 && k <= n, "need 1 <= nev, 1 <= nex, nev + nex <= n");
+    CHFSI_REQUIRE(tol > 0.0, "tol must be > 0");
+    mixed = o->precision == CHFSI_PREC_MIXED;
+    tc_all = o->precision == CHFSI_PREC_TC;
+    if ((mixed || tc_all) && !tc_filter_supported(ctx))
+      throw ChfsiError{CHFSI_ENOTSUP, "split-precision filter needs an sm_103 device"};
+    std::memset(&S, 0, sizeof(S));
+    launches0 = chfsi_launch_counter();
+    for (auto& e : ev) CHFSI_CUDA_TRY(cudaEventCreate(&e));
+    mark(0);
+    const size_t blk = sizeof(double2) * (size_t)n * k;
+    Xact = (double2*)ws("s_Xact", blk);
+    Yf = (double2*)ws("s_Yf", blk);
+    Yrr = (double2*)ws("s_Yrr", blk);
+    HY = (double2*)ws("s_HY", blk);
+    Lk = (double2*)ws("s_Lk", sizeof(double2) * (size_t)n * nev);
+    lam = (double*)ws("s_lam", sizeof(double) * k);
+    res = (double*)ws("s_res", sizeof(double) * k);
+    lamL = (double*)ws("s_lamL", sizeof(double) * nev);
+    resL = (double*)ws("s_resL", sizeof(double) * nev);
+    Rblk = tc_all ? (double2*)ws("s_Rblk", blk) : nullptr;
+    lam_act = (double*)ws("s_lamact", sizeof(double) * k);
+    int* iws = (int*)ws("s_int", sizeof(int) * 5 * (size_t)k);
+    lock_idx = iws;
+    act_idx = iws + k;
+    deg = iws + 2 * k;
+    perm = iws + 3 * k;
+    deg_sorted = iws + 4 * k;
+    bnd = (double*)ws("s_bnd", sizeof(double) * 4);
+    ctl = (LoopCtl*)ws("s_ctl", sizeof(LoopCtl));
+    char* hp = (char*)pinned_get(ctx, 1024 + sizeof(int) * (size_t)k + sizeof(double) * k);
+    double* bnd_h = (double*)(hp + 512);
+
+    if (any_nonfinite(ctx, (size_t)2 * n * k, (const double*)X))
+      throw ChfsiError{CHFSI_ENAN, "NaN/Inf in the starting block"};
+    if (any_nonfinite(ctx, (size_t)2 * n * n, (const double*)H))
+      throw ChfsiError{CHFSI_ENAN, "NaN/Inf in H"};
+    // Alg. 1 line 3: bounds of the spectrum.
+    lanczos_dev(ctx, H, n, o->lanczos_steps, o->seed, bnd);
+    CHFSI_CUDA_TRY(cudaMemcpyAsync(bnd_h, bnd, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
+    mark(1);
+    CHFSI_CUDA_TRY(cudaStreamSynchronize(st));
+    S.ms_lanczos = ms(0, 1);
+    beta = bnd_h[0];
+    norm_h = bnd_h[3];
+    if (!std::isfinite(beta) || !std::isfinite(norm_h) || norm_h <= 0.0)
+      throw ChfsiError{CHFSI_ENAN, "Lanczos bounds are not finite"};
+    S.beta = beta;
+    S.norm_h = norm_h;
+    int deg0;
+    if (warm) {
+      gamma = warm[0];
+      alpha = warm[1];
+      deg0 = o->deg_warm;
     } else {
-      filter_f64(ctx, H, n, ka, Xact, degs.data(), gamma, c, e, Yf);
+      gamma = bnd_h[1];
+      alpha = gamma + (beta - gamma) * (double)k / (double)n;
+      deg0 = o->deg_cold;
+    }
+    CHFSI_REQUIRE(alpha < beta, "filter interval is empty (alpha >= beta)");
+    copy_columns(st, n, k, X, n, Xact, n);
+    degs.assign(k, deg0);
+    ka = k;
+    nl = 0;
+    use_mlp = o->degree_model == CHFSI_DEG_MLP;
+    trace_abandon(ctx);
+    lowp_on = mixed;
+  }
+
+  double c_() const { return 0.5 * (alpha + beta); }
+  double e_() const { return 0.5 * (beta - alpha); }
+
+  // Start of a loop: which filter this problem's loop uses.
+  enum FilterKind { F64 = 0, TC_PLAIN = 1, TC_DEFECT = 2 };
+  FilterKind begin_loop() {
+    ++loops;
+    if (lowp_on && !(max_resid_wanted > o->switch_tol)) lowp_on = false;
+    sdeg = 0;
+    for (int j = 0; j < ka; ++j) sdeg += degs[j];
+    mark(2);
+    fl0 = chfsi_launch_counter();
+    if (tc_all) return loops == 1 ? TC_PLAIN : TC_DEFECT;
+    if (lowp_on) return TC_PLAIN;
+    return F64;
+  }
+
+  // The filter of this loop run by this problem alone.
+  void filter_single(FilterKind kind) {
+    if (kind == TC_PLAIN)
+      tc_filter_run(ctx, H, n, ka, Xact, degs.data(), gamma, c_(), e_(), Yf);
+    else if (kind == TC_DEFECT)
+      tc_filter_run_defect(ctx, H, n, ka, Xact, Rblk, lam_act, degs.data(), deg_sorted, gamma,
+                           c_(), e_(), Yf);
+    else
+      filter_f64(ctx, H, n, ka, Xact, degs.data(), gamma, c_(), e_(), Yf);
+  }
+
+  // Work item of this loop's filter for a batched launch.
+  TcBatchItem batch_item(FilterKind kind) {
+    TcBatchItem it;
+    it.H = H;
+    it.n = n;
+    it.k = ka;
+    it.src = Xact;
+    it.R = nullptr;
+    it.fR = nullptr;
+    it.deg = degs.data();
+    it.lam1 = gamma;
+    it.c = c_();
+    it.e = e_();
+    it.out = Yf;
+    if (kind == TC_DEFECT) {
+      tc_defect_tables(ctx, pre, ka, lam_act, degs.data(), gamma, c_(), e_(), &psi, &fR);
+      it.R = Rblk;
+      it.fR = fR;
+    }
+    return it;
+  }
+  void after_batch(FilterKind kind) {
+    if (kind == TC_DEFECT) tc_defect_combine(st, n, ka, Xact, deg_sorted, psi, Yf);
+  }
+
+  // Rest of the loop; sets done when nev pairs are locked.
+  void post(FilterKind kind) {
+    if (kind != F64) {
+      S.loops_lowp++;
+      S.col_degrees_lowp += sdeg;
     }
     S.col_degrees += sdeg;
     S.filter_launches += chfsi_launch_counter() - fl0;
-    tm.mark(3);
+    mark(3);
     orthonormalize_dev(ctx, n, nl, Lk, ka, Yf);
-    tm.mark(4);
+    mark(4);
     rayleigh_ritz_dev(ctx, H, n, ka, Yf, Yrr, HY, lam);
-    tm.mark(5);
+    mark(5);
     residual_norms(st, n, ka, HY, Yrr, lam, norm_h, res);
     trace_finish(ctx, ka, res);
-    tm.mark(6);
+    mark(6);
     lock_select(st, ka, lam, res, nev - nl, tol, gamma, ctl, lock_idx, act_idx);
+    char* hp = (char*)pinned_get(ctx, 1024 + sizeof(int) * (size_t)k + sizeof(double) * k);
+    LoopCtl* ctl_h = (LoopCtl*)(hp + 256);
+    int* deg_h = (int*)(hp + 1024);
     CHFSI_CUDA_TRY(cudaMemcpyAsync(ctl_h, ctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, st));
     CHFSI_CUDA_TRY(cudaStreamSynchronize(st));
     if (ctl_h->nonfinite) throw ChfsiError{CHFSI_ENAN, "NaN/Inf in Ritz values or residuals"};
@@ -523,18 +588,19 @@ int solve_one(chfsi_ctx* ctx, const double2* H, int n, int nev, int nex, double2
     max_resid_wanted = ctl_h->max_resid_wanted;
     if (nl >= nev) {
       status = CHFSI_OK;
-      tm.mark(7);
+      done = true;
+      mark(7);
       CHFSI_CUDA_TRY(cudaStreamSynchronize(st));
     } else {
       alpha = ctl_h->alpha;
-      const double c2 = 0.5 * (alpha + beta), e2 = 0.5 * (beta - alpha);
+      const double c2 = c_(), e2 = e_();
       if (use_mlp) {
         mlp_degrees(ctx, ka, lam, res, act_idx, c2, e2, gamma, step, tol, deg);
         degree_cap_buffer(st, ka, nev - nl, deg);
         S.loops_mlp++;
       } else {
-        degrees_analytic(st, ka, lam, res, act_idx, c2, e2, tol, nev - nl, o.deg_min,
-                         o.deg_max, o.deg_extra, deg);
+        degrees_analytic(st, ka, lam, res, act_idx, c2, e2, tol, nev - nl, o->deg_min,
+                         o->deg_max, o->deg_extra, deg);
       }
       trace_record(ctx, ka, lam, res, act_idx, deg, c2, e2, gamma, step, nev - nl);
       sort_by_degree(st, ka, deg, act_idx, perm, deg_sorted);
@@ -542,49 +608,144 @@ int solve_one(chfsi_ctx* ctx, const double2* H, int n, int nev, int nex, double2
       if (tc_all) residual_block(st, n, ka, HY, Yrr, lam, perm, Rblk, lam_act);
       CHFSI_CUDA_TRY(cudaMemcpyAsync(deg_h, deg_sorted, sizeof(int) * ka,
                                      cudaMemcpyDeviceToHost, st));
-      tm.mark(7);
+      mark(7);
       CHFSI_CUDA_TRY(cudaStreamSynchronize(st));
       degs.assign(deg_h, deg_h + ka);
+      if (loops >= o->max_loops) done = true;
     }
-    if (o.profile) kt_resolve(&timer);
-    S.ms_filter += tm.ms(2, 3);
-    S.ms_qr += tm.ms(3, 4);
-    S.ms_rr += tm.ms(4, 5);
-    S.ms_resid += tm.ms(5, 6);
-    S.ms_lock += tm.ms(6, 7);
-    if (status == CHFSI_OK) break;
+    S.ms_filter += ms(2, 3);
+    S.ms_qr += ms(3, 4);
+    S.ms_rr += ms(4, 5);
+    S.ms_resid += ms(5, 6);
+    S.ms_lock += ms(6, 7);
   }
+
   // Output: locked pairs ascending, then the remaining active block.
-  int* permL = perm;
-  sort_by_value(st, nl, lamL, permL);
-  gather_columns(st, n, nl, Lk, n, permL, X, n);
-  gather_values(st, nl, lamL, permL, evals_out);
-  gather_columns(st, n, ka, Yrr, n, act_idx, X + (size_t)nl * n, n);
-  gather_values(st, ka, lam, act_idx, evals_out + nl);
-  double* rl_h = (double*)(hp + 1024);
-  CHFSI_CUDA_TRY(cudaMemcpyAsync(rl_h, resL, sizeof(double) * std::max(nl, 1),
-                                 cudaMemcpyDeviceToHost, st));
-  tm.mark(8);
-  CHFSI_CUDA_TRY(cudaStreamSynchronize(st));
-  double mr = 0.0;
-  for (int j = 0; j < std::min(nl, nev); ++j) mr = std::max(mr, rl_h[j]);
-  S.max_resid = (nl >= nev) ? mr : INFINITY;
-  S.loops = loops;
-  S.n_locked = nl;
-  S.status = status;
-  S.ms_total = tm.ms(0, 8);
-  S.filter_flops = 8.0 * (double)n * (double)n * (double)S.col_degrees;
-  S.launches = chfsi_launch_counter() - launches0;
-  if (o.profile) {
-    kt_resolve(&timer);
-    S.k_f64_ms = timer.ms[KT_F64];
-    S.k_f64_flops = timer.fl[KT_F64];
-    S.k_f64_launches = timer.n[KT_F64];
-    S.k_tc_ms = timer.ms[KT_TC];
-    S.k_tc_flops = timer.fl[KT_TC];
-    S.k_tc_launches = timer.n[KT_TC];
+  int finish() {
+    int* permL = perm;
+    sort_by_value(st, nl, lamL, permL);
+    gather_columns(st, n, nl, Lk, n, permL, X, n);
+    gather_values(st, nl, lamL, permL, evals_out);
+    gather_columns(st, n, ka, Yrr, n, act_idx, X + (size_t)nl * n, n);
+    gather_values(st, ka, lam, act_idx, evals_out + nl);
+    char* hp = (char*)pinned_get(ctx, 1024 + sizeof(int) * (size_t)k + sizeof(double) * k);
+    double* rl_h = (double*)(hp + 1024);
+    CHFSI_CUDA_TRY(cudaMemcpyAsync(rl_h, resL, sizeof(double) * std::max(nl, 1),
+                                   cudaMemcpyDeviceToHost, st));
+    mark(8);
+    CHFSI_CUDA_TRY(cudaStreamSynchronize(st));
+    double mr = 0.0;
+    for (int j = 0; j < std::min(nl, nev); ++j) mr = std::max(mr, rl_h[j]);
+    S.max_resid = (nl >= nev) ? mr : INFINITY;
+    S.loops = loops;
+    S.n_locked = nl;
+    S.status = status;
+    S.ms_total = ms(0, 8);
+    S.filter_flops = 8.0 * (double)n * (double)n * (double)S.col_degrees;
+    S.launches = chfsi_launch_counter() - launches0;
+    return status;
   }
-  if (stats) *stats = S;
+};
+
+void copy_kernel_times(chfsi_stats& S, const KernelTimer& t) {
+  S.k_f64_ms = t.ms[KT_F64];
+  S.k_f64_flops = t.fl[KT_F64];
+  S.k_f64_launches = t.n[KT_F64];
+  S.k_tc_ms = t.ms[KT_TC];
+  S.k_tc_flops = t.fl[KT_TC];
+  S.k_tc_launches = t.n[KT_TC];
+}
+
+struct TimerScope {
+  KernelTimer* t;
+  explicit TimerScope(KernelTimer* x) : t(x) { kt_install(x); }
+  ~TimerScope() {
+    kt_install(nullptr);
+    if (t)
+      for (auto e : t->ev) cudaEventDestroy(e);
+  }
+};
+
+int solve_one(chfsi_ctx* ctx, const double2* H, int n, int nev, int nex, double2* X,
+              double tol, double* evals_out, const double* warm, chfsi_stats* stats,
+              int step) {
+  KernelTimer timer;
+  TimerScope scope(ctx->opts.profile ? &timer : nullptr);
+  Problem pb;
+  pb.init(ctx, "", H, n, nev, nex, X, tol, evals_out, warm, stats, step);
+  while (!pb.done && pb.loops < ctx->opts.max_loops) {
+    const Problem::FilterKind kind = pb.begin_loop();
+    pb.filter_single(kind);
+    pb.post(kind);
+    if (ctx->opts.profile) kt_resolve(&timer);
+  }
+  const int status = pb.finish();
+  if (ctx->opts.profile) {
+    kt_resolve(&timer);
+    copy_kernel_times(pb.S, timer);
+  }
+  if (stats) *stats = pb.S;
+  return status;
+}
+
+// P independent problems in lockstep: one batched tensor-core filter launch
+// per loop for every problem whose loop uses the split-precision filter,
+// then each problem's QR, Rayleigh-Ritz and locking.
+int solve_batch(chfsi_ctx* ctx, int P, const double2* const* H, const int* n, const int* nev,
+                const int* nex, double2* const* X, double tol, double* const* evals,
+                const double* warm /* 2P or null */, chfsi_stats* stats, int step,
+                double* ms_filter_total) {
+  KernelTimer timer;
+  TimerScope scope(ctx->opts.profile ? &timer : nullptr);
+  std::vector<Problem> pbs(P);
+  for (int p = 0; p < P; ++p)
+    pbs[p].init(ctx, "b" + std::to_string(p) + ".", H[p], n[p], nev[p], nex[p], X[p], tol,
+                evals[p], warm ? warm + 2 * p : nullptr, stats ? stats + p : nullptr, step);
+  cudaEvent_t e0, e1;
+  CHFSI_CUDA_TRY(cudaEventCreate(&e0));
+  CHFSI_CUDA_TRY(cudaEventCreate(&e1));
+  double filt_ms = 0.0;
+  for (;;) {
+    std::vector<int> act;
+    for (int p = 0; p < P; ++p)
+      if (!pbs[p].done && pbs[p].loops < ctx->opts.max_loops) act.push_back(p);
+    if (act.empty()) break;
+    std::vector<Problem::FilterKind> kind(P, Problem::F64);
+    std::vector<TcBatchItem> items;
+    std::vector<int> in_batch;
+    for (int p : act) {
+      kind[p] = pbs[p].begin_loop();
+      if (kind[p] != Problem::F64) {
+        items.push_back(pbs[p].batch_item(kind[p]));
+        in_batch.push_back(p);
+      }
+    }
+    CHFSI_CUDA_TRY(cudaEventRecord(e0, ctx->stream));
+    if (!items.empty()) tc_filter_batched_run(ctx, (int)items.size(), items.data());
+    for (int p : in_batch) pbs[p].after_batch(kind[p]);
+    for (int p : act)
+      if (kind[p] == Problem::F64) pbs[p].filter_single(kind[p]);
+    CHFSI_CUDA_TRY(cudaEventRecord(e1, ctx->stream));
+    CHFSI_CUDA_TRY(cudaEventSynchronize(e1));
+    float t = 0.f;
+    CHFSI_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+    filt_ms += t;
+    for (int p : act) pbs[p].post(kind[p]);
+    if (ctx->opts.profile) kt_resolve(&timer);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int status = CHFSI_OK;
+  for (int p = 0; p < P; ++p) {
+    const int s = pbs[p].finish();
+    if (s != CHFSI_OK && status == CHFSI_OK) status = s;
+    if (stats) stats[p] = pbs[p].S;
+  }
+  if (ctx->opts.profile && stats && P > 0) {
+    kt_resolve(&timer);
+    copy_kernel_times(stats[0], timer);  // batch totals reported on problem 0
+  }
+  if (ms_filter_total) *ms_filter_total = filt_ms;
   return status;
 }
 
@@ -783,6 +944,50 @@ int chfsi_solve_sequence_host(chfsi_ctx* ctx, const double* const* H, int N, int
     CHFSI_CUDA_TRY(cudaMemcpyAsync(evals_host, Ed, sizeof(double) * (size_t)N * k,
                                    cudaMemcpyDeviceToHost, ctx->stream));
     CHFSI_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  });
+  return rc != CHFSI_OK ? rc : status;
+}
+
+int chfsi_solve_batched(chfsi_ctx* ctx, int P, const chfsi_problem* probs, int steps,
+                        double tol, chfsi_stats* stats) {
+  if (!ctx) return CHFSI_EINVAL;
+  int status = CHFSI_OK;
+  int rc = run_guarded(ctx, [&] {
+    CHFSI_REQUIRE(P >= 1 && probs && steps >= 1, "bad batched arguments");
+    std::vector<const double2*> H(P);
+    std::vector<int> n(P), nev(P), nex(P);
+    std::vector<double2*> X(P);
+    std::vector<double*> ev(P);
+    std::vector<double> warm(2 * (size_t)P);
+    for (int p = 0; p < P; ++p) {
+      CHFSI_REQUIRE(probs[p].H_host && probs[p].X && probs[p].evals, "NULL in a problem");
+      n[p] = probs[p].n;
+      nev[p] = probs[p].nev;
+      nex[p] = probs[p].nex;
+      X[p] = C2(probs[p].X);
+    }
+    for (int l = 0; l < steps; ++l) {
+      for (int p = 0; p < P; ++p) {
+        H[p] = C2(probs[p].H_host[l]);
+        CHFSI_REQUIRE(H[p] != nullptr, "NULL H in a batched sequence");
+        ev[p] = probs[p].evals + (size_t)l * (nev[p] + nex[p]);
+      }
+      const int s = solve_batch(ctx, P, H.data(), n.data(), nev.data(), nex.data(), X.data(),
+                                tol, ev.data(), l ? warm.data() : nullptr,
+                                stats ? stats + (size_t)l * P : nullptr, ctx->opts.step0 + l,
+                                nullptr);
+      if (s != CHFSI_OK && status == CHFSI_OK) status = s;
+      double* wh = (double*)pinned_get(ctx, sizeof(double) * 2 * (size_t)P + 64);
+      for (int p = 0; p < P; ++p) {
+        const int k = nev[p] + nex[p];
+        CHFSI_CUDA_TRY(cudaMemcpyAsync(wh + 2 * p, ev[p], sizeof(double),
+                                       cudaMemcpyDeviceToHost, ctx->stream));
+        CHFSI_CUDA_TRY(cudaMemcpyAsync(wh + 2 * p + 1, ev[p] + k - 1, sizeof(double),
+                                       cudaMemcpyDeviceToHost, ctx->stream));
+      }
+      CHFSI_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+      std::copy(wh, wh + 2 * P, warm.begin());
+    }
   });
   return rc != CHFSI_OK ? rc : status;
 }

@@ -215,6 +215,11 @@ struct TcBatchItem {
   double2* out;
 };
 void tc_filter_batched_run(chfsi_ctx* ctx, int P, const TcBatchItem* items);
+void tc_defect_tables(chfsi_ctx* ctx, const std::string& prefix, int k, const double* lam,
+                      const int* deg_host, double lam1, double c, double e, double** psi,
+                      double** fR);
+void tc_defect_combine(cudaStream_t st, int n, int k, const double2* Y, const int* deg_dev,
+                       const double* psi, double2* out);
 void tc_filter_batched_release(chfsi_ctx* ctx);
 // R[:, j] = HY[:, perm[j]] - lam[perm[j]] Y[:, perm[j]], lam_out[j] = lam[perm[j]].
 void residual_block(cudaStream_t st, int n, int k, const double2* HY, const double2* Y,

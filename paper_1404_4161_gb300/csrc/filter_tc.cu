@@ -518,15 +518,13 @@ void tc_filter_run(chfsi_ctx* ctx, const double2* H, int n, int k, const double2
   run_filter(ctx, H, n, k, Y0, nullptr, nullptr, deg_host, lam1, c, e, Yout);
 }
 
-// Defect form: Y (Ritz vectors, degree-sorted), R = HY - Y Lambda (same
-// order), lam (Ritz values, device, same order), deg_dev (device copy of
-// the degrees).  Yout = p(H) Y per column.
-void tc_filter_run_defect(chfsi_ctx* ctx, const double2* H, int n, int k, const double2* Y,
-                          const double2* Rres, const double* lam, const int* deg_host,
-                          const int* deg_dev, double lam1, double c, double e, double2* Yout) {
+// Refinement-form tables for one problem: psi[i][j] = psi_i(lambda_j) and
+// the forcing coefficients fR[i][j] = a_i psi_i(lambda_j), (m_k + 1) x k each,
+// in context workspaces named after `prefix`.
+void tc_defect_tables(chfsi_ctx* ctx, const std::string& prefix, int k, const double* lam,
+                      const int* deg_host, double lam1, double c, double e, double** psi_out,
+                      double** fR_out) {
   const int mk = deg_host[k - 1];
-  // Recurrence coefficients a_0; (a_i, b_i) i >= 1, and the psi table whose
-  // row i holds the forcing coefficient a_i psi_i(lambda_j) for step i.
   std::vector<double> coef(2 * mk + 1, 0.0);
   const double sigma1 = e / (lam1 - c);
   coef[0] = sigma1 / e;
@@ -537,24 +535,44 @@ void tc_filter_run_defect(chfsi_ctx* ctx, const double2* H, int n, int k, const 
     coef[2 * i] = -sn * sigma;
     sigma = sn;
   }
-  double* dcoef = (double*)ws_get(ctx, "tc_coef", sizeof(double) * coef.size());
-  double* psi = (double*)ws_get(ctx, "tc_psi", sizeof(double) * (size_t)(mk + 1) * k);
-  double* fR = (double*)ws_get(ctx, "tc_fR", sizeof(double) * (size_t)(mk + 1) * k);
-  CHFSI_CUDA_TRY(cudaMemcpyAsync(dcoef, coef.data(), sizeof(double) * coef.size(),
+  std::vector<double> ai(mk + 1, 0.0);
+  for (int i = 1; i < mk; ++i) ai[i] = coef[2 * i - 1];
+  double* dcoef = (double*)ws_get(ctx, (prefix + "tc_coef").c_str(), sizeof(double) * coef.size());
+  double* dai = (double*)ws_get(ctx, (prefix + "tc_ai").c_str(), sizeof(double) * (mk + 1));
+  double* psi = (double*)ws_get(ctx, (prefix + "tc_psi").c_str(), sizeof(double) * (size_t)(mk + 1) * k);
+  double* fR = (double*)ws_get(ctx, (prefix + "tc_fR").c_str(), sizeof(double) * (size_t)(mk + 1) * k);
+  double* hbuf = (double*)pinned_get(ctx, sizeof(double) * (coef.size() + ai.size()) + 64);
+  std::copy(coef.begin(), coef.end(), hbuf);
+  std::copy(ai.begin(), ai.end(), hbuf + coef.size());
+  CHFSI_CUDA_TRY(cudaMemcpyAsync(dcoef, hbuf, sizeof(double) * coef.size(),
+                                 cudaMemcpyHostToDevice, ctx->stream));
+  CHFSI_CUDA_TRY(cudaMemcpyAsync(dai, hbuf + coef.size(), sizeof(double) * ai.size(),
                                  cudaMemcpyHostToDevice, ctx->stream));
   psi_table_kernel<<<(k + 127) / 128, 128, 0, ctx->stream>>>(k, mk, lam, c, dcoef, psi);
   chfsi_check_launch("psi_table");
-  // forcing coefficients fR[i][j] = a_i psi_i(lambda_j)
-  std::vector<double> ai(mk + 1, 0.0);
-  for (int i = 1; i < mk; ++i) ai[i] = coef[2 * i - 1];
-  double* dai = (double*)ws_get(ctx, "tc_ai", sizeof(double) * (mk + 1));
-  CHFSI_CUDA_TRY(cudaMemcpyAsync(dai, ai.data(), sizeof(double) * (mk + 1),
-                                 cudaMemcpyHostToDevice, ctx->stream));
   scale_rows_kernel<<<(unsigned)(((size_t)(mk + 1) * k + 255) / 256), 256, 0, ctx->stream>>>(
       mk + 1, k, psi, dai, fR);
   chfsi_check_launch("scale_rows");
-  run_filter(ctx, H, n, k, Y, Rres, fR, deg_host, lam1, c, e, Yout);
-  defect_combine_kernel<<<dim3((n + 255) / 256, k), 256, 0, ctx->stream>>>(n, k, Y, deg_dev,
-                                                                          psi, Yout);
+  // the host staging buffer is reused by the next call: finish the copies
+  CHFSI_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  *psi_out = psi;
+  *fR_out = fR;
+}
+
+void tc_defect_combine(cudaStream_t st, int n, int k, const double2* Y, const int* deg_dev,
+                       const double* psi, double2* out) {
+  defect_combine_kernel<<<dim3((n + 255) / 256, k), 256, 0, st>>>(n, k, Y, deg_dev, psi, out);
   chfsi_check_launch("defect_combine");
+}
+
+// Defect form: Y (Ritz vectors, degree-sorted), R = HY - Y Lambda (same
+// order), lam (Ritz values, device, same order), deg_dev (device copy of
+// the degrees).  Yout = p(H) Y per column.
+void tc_filter_run_defect(chfsi_ctx* ctx, const double2* H, int n, int k, const double2* Y,
+                          const double2* Rres, const double* lam, const int* deg_host,
+                          const int* deg_dev, double lam1, double c, double e, double2* Yout) {
+  double *psi, *fR;
+  tc_defect_tables(ctx, "", k, lam, deg_host, lam1, c, e, &psi, &fR);
+  run_filter(ctx, H, n, k, Y, Rres, fR, deg_host, lam1, c, e, Yout);
+  tc_defect_combine(ctx->stream, n, k, Y, deg_dev, psi, Yout);
 }

@@ -97,6 +97,28 @@ class Chfsi:
         self._check(rc, allow)
         return ev, [s.as_dict() for s in st], rc
 
+    def solve_batched(self, seqs, tol, allow=(L.ENOCONV,)):
+        """seqs: list of (list of Hc per step, nev, nex, Xc); all sequences
+        have the same number of steps.  Returns (evals per problem, stats
+        [step][problem], rc)."""
+        P = len(seqs)
+        steps = len(seqs[0][0])
+        probs = (L.Problem * P)()
+        keep, evs = [], []
+        for p, (Hcs, nev, nex, Xc) in enumerate(seqs):
+            ptrs = (C.c_void_p * steps)(*[h.data_ptr() for h in Hcs])
+            keep.append(ptrs)
+            ev = torch.empty((steps, nev + nex), dtype=torch.float64, device=Xc.device)
+            evs.append(ev)
+            probs[p] = L.Problem(C.cast(ptrs, C.c_void_p), Hcs[0].shape[0], nev, nex,
+                                 Xc.data_ptr(), ev.data_ptr())
+        st = (Stats * (P * steps))()
+        rc = self.lib.chfsi_solve_batched(self.ctx, P, C.cast(probs, C.c_void_p), steps, tol,
+                                          C.cast(st, C.c_void_p))
+        self._check(rc, allow)
+        stats = [[st[l * P + p].as_dict() for p in range(P)] for l in range(steps)]
+        return evs, stats, rc
+
     # -- single steps -------------------------------------------------
     def lanczos(self, Hc, steps, seed):
         out = (C.c_double * 4)()

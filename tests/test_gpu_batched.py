@@ -74,3 +74,35 @@ def test_batched_twice_and_many_problems(ctx):
             single = from_dev_cm(ctx.filter(Hc, Y0c, degrees, lam1, c, e,
                                             precision=L.PREC_MIXED))
             assert colrel(from_dev_cm(out), single) < 1e-6
+
+
+def test_solve_batched_sequences():
+    """Six independent correlated sequences of uneven size (delta = 0, so
+    every step has its problem's known spectrum), two steps, solved in
+    lockstep with one batched filter launch per loop."""
+    from paper_1404_4161_gb300.build import build
+    from workloads.synthetic import BASE_SEED, CONFIGS, config_sequence
+    build()
+    cfg = CONFIGS[4]
+    sizes = [(320, 20, 5), (448, 28, 7), (512, 32, 8), (600, 37, 9), (384, 24, 6), (700, 43, 10)]
+    seqs, ref = [], []
+    for i, (n, nev, nex) in enumerate(sizes):
+        Hs, lam = config_sequence(cfg, BASE_SEED + 4000 + i, length=2, n=n, eps=1e-3, delta=0.0)
+        X0 = random_block(n, nev + nex, BASE_SEED + 4500 + i)
+        seqs.append(([to_dev_cm(h) for h in Hs], nev, nex, to_dev_cm(X0)))
+        ref.append((Hs, lam, nev))
+    s = Chfsi(precision=L.PREC_TC)
+    evs, stats, rc = s.solve_batched(seqs, 1e-10)
+    s.close()
+    assert rc == L.OK
+    for (Hcs, nev, nex, Xc), ev, (Hs, lam, nev_) in zip(seqs, evs, ref):
+        ev = ev.cpu().numpy()
+        normH = np.abs(lam).max()
+        for l in range(2):
+            assert np.abs(ev[l, :nev] - lam[:nev]).max() <= 1e-12 * normH
+        X = from_dev_cm(Xc)
+        R = np.linalg.norm(Hs[-1] @ X[:, :nev] - X[:, :nev] * ev[-1, :nev], axis=0) / normH
+        assert R.max() <= 1e-10
+    for l in range(2):
+        for st in stats[l]:
+            assert st["status"] == L.OK and st["loops_lowp"] == st["loops"]

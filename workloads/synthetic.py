@@ -158,7 +158,13 @@ def config_problem(cfg: Config, seed: int, n: int | None = None, device=None):
     ``n`` overrides the size (the spectrum layout scales with it)."""
     n = cfg.n if n is None else n
     rng = _rng(seed)
-    n_low = cfg.n_low if n == cfg.n else max(1, int(round(cfg.n_low * n / cfg.n)))
+    if cfg.n == 0:  # per-problem sizes (batched): nev = n/16, nex = nev/4
+        nev = max(1, n // 16)
+        n_low = nev + max(1, nev // 4) // 2
+    elif n == cfg.n:
+        n_low = cfg.n_low
+    else:
+        n_low = max(1, int(round(cfg.n_low * n / cfg.n)))
     lam = two_band_spectrum(n, n_low, cfg.low, cfg.bulk, rng)
     q = haar_unitary(n, rng, device=device)
     return hermitian_from_spectrum(lam, q), lam
