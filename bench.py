@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--degrees", choices=["learned", "analytic"], default="learned")
+    ap.add_argument("--f64-gemm", choices=["ozaki", "fp64"], default="ozaki",
+                    help="engine of the FP64 products in the tc/mixed modes")
     ap.add_argument("--batched-scale", type=float, default=0.25,
                     help="n range of the 64-problem batched measurement, as a fraction of "
                          "[1500, 6000] (0 skips it)")
@@ -270,7 +272,8 @@ def main():
     torch.cuda.synchronize()
 
     prec = {"tc": L.PREC_TC, "mixed": L.PREC_MIXED, "fp64": L.PREC_FP64}[args.precision]
-    s = Chfsi(precision=prec, profile=1)
+    f64g = L.GEMM_OZAKI if (args.f64_gemm == "ozaki" and prec != L.PREC_FP64) else L.GEMM_FP64
+    s = Chfsi(precision=prec, profile=1, f64_gemm=f64g)
     stream = torch.cuda.current_stream()
     train_info = None
     if args.degrees == "learned":
@@ -351,12 +354,19 @@ def main():
     f64_roof = None
     if k64_ms > 0:
         a = k64_fl / (k64_ms / 1e3) / 1e12
-        f64_roof = {"bound": "alu", "achieved": a, "peak": FP64_PEAK, "unit": "TFLOP/s",
-                    "frac": a / FP64_PEAK, "traffic": None,
-                    "kernel": "zgemm_nn_kernel + zgemm_cn_part_kernel (FP64 complex GEMMs)",
+        oz = f64g == L.GEMM_OZAKI
+        f64_roof = {"bound": "tensor" if oz else "alu",
+                    "achieved": 21.0 * a if oz else a,
+                    "peak": bf16_peak if oz else FP64_PEAK, "unit": "TFLOP/s",
+                    "frac": (21.0 * a / bf16_peak) if oz else a / FP64_PEAK, "traffic": None,
+                    "fp64_equivalent_tflops": a,
+                    "kernel": ("oz_gemm_kernel (FP64-accurate complex GEMM, 21 BF16 slice "
+                               "products per product)") if oz else
+                              "zgemm_nn_kernel + zgemm_cn_part_kernel (FP64 complex GEMMs)",
                     "launches": int(k64_n), "avg_launch_ms": k64_ms / max(k64_n, 1),
-                    "peak_source": "measured FP64 GEMM rate on this GB300 (no FP64 entry in "
-                                   "MEASURED_PEAKS.json)"}
+                    "peak_source": ("bf16_tflops_sustained of measured" if oz else
+                                    "measured FP64 GEMM rate on this GB300 (no FP64 entry in "
+                                    "MEASURED_PEAKS.json)")}
     tc_roof = None
     if ktc_ms > 0:
         a = 3.0 * ktc_fl / (ktc_ms / 1e3) / 1e12  # three BF16 products per complex product
@@ -439,6 +449,7 @@ def main():
                                    f"problems, n={n}, nev={nev}, nex={nex}, eps=1e-3, "
                                    f"delta=1e-4, tol 1e-10",
                        "precision": args.precision, "degree_model": args.degrees,
+                       "f64_products": "ozaki (tensor cores)" if f64g == L.GEMM_OZAKI else "fp64 pipe",
                        "l2": "inputs larger than L2 (each H is 16 n^2 bytes)",
                        "parallelism": f"replicas x{ws}"},
             "filter_tflops": filter_tflops,

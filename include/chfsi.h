@@ -56,6 +56,13 @@ extern "C" {
 #define CHFSI_SPLIT_BF16X3 0 /* x = hi + lo in bf16; hi*hi + hi*lo + lo*hi   */
 #define CHFSI_SPLIT_FP16X3 1 /* same with fp16 and a power-of-two scaling    */
 
+/* Engine of the FP64 products (H Q, Gram matrices, block products). */
+#define CHFSI_GEMM_FP64 0   /* DFMA kernels on the FP64 pipe                 */
+#define CHFSI_GEMM_OZAKI 1  /* FP64-accurate emulation on the BF16 tensor    */
+                            /* cores: 6 x 7-bit error-free slices, 21 slice  */
+                            /* products, exact FP32 chunk sums (~2^-42 of    */
+                            /* row scale x column scale per product)         */
+
 /* Degree model (Alg. 1 line 11). */
 #define CHFSI_DEG_ANALYTIC 0 /* Single Optimization rule of Sec. 3.2         */
 #define CHFSI_DEG_MLP 1      /* learned predictor; analytic rule as fallback */
@@ -80,6 +87,7 @@ typedef struct chfsi_opts {
   int mlp_extra;       /* DEG_MLP: margin added to the learned degree (2) */
   int step0;           /* sequence index of the next problem solved (0):  */
                        /* the step feature of the degree MLP and traces   */
+  int f64_gemm;        /* CHFSI_GEMM_FP64 / CHFSI_GEMM_OZAKI        (FP64) */
 } chfsi_opts;
 
 /* Per-problem statistics (host struct, filled when non-NULL). */
@@ -239,6 +247,14 @@ int chfsi_filter_batched(chfsi_ctx* ctx, int P, const chfsi_filter_item* items);
 int chfsi_filter_refine(chfsi_ctx* ctx, const double* H, int n, int k, const double* Y,
                         const double* R, const double* ritz, const int* degrees_host,
                         double lam1, double c, double e, double* Yout);
+
+/* Complex GEMM with either engine: C = alpha op(A) B + beta C, op(A) = A
+ * (op_a = 0) or A^H (op_a = 1); op(A) is m x k, B k x n, C m x n, all
+ * column-major complex with leading dimensions lda, ldb, ldc (device).
+ * engine = CHFSI_GEMM_FP64 or CHFSI_GEMM_OZAKI.  The building block of
+ * Rayleigh-Ritz (H Q, Q^H Z, Q W) and CholQR (Y^H Y, Y R^-1). */
+int chfsi_zgemm(chfsi_ctx* ctx, int op_a, int m, int n, int k, double alpha, const double* A,
+                int lda, const double* B, int ldb, double beta, double* C, int ldc, int engine);
 
 /* Alg. 1 line 6: orthonormalise the k columns of Y (complex n x k, in
  * place) against the nl orthonormal columns of L (complex n x nl; may be

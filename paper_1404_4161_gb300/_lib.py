@@ -16,6 +16,7 @@ FILTER_STATIC_MAX_NK = 262144
 PREC_FP64, PREC_MIXED, PREC_TC = 0, 1, 2
 SPLIT_BF16X3, SPLIT_FP16X3 = 0, 1
 DEG_ANALYTIC, DEG_MLP = 0, 1
+GEMM_FP64, GEMM_OZAKI = 0, 1
 MLP_NPARAM = 64 * 5 + 64 + 64 * 64 + 64 + 64 + 1
 
 
@@ -24,7 +25,8 @@ class Opts(C.Structure):
                 ("deg_cold", C.c_int), ("deg_warm", C.c_int), ("deg_min", C.c_int),
                 ("deg_max", C.c_int), ("deg_extra", C.c_int), ("lanczos_steps", C.c_int),
                 ("max_loops", C.c_int), ("switch_tol", C.c_double), ("seed", C.c_ulonglong),
-                ("profile", C.c_int), ("mlp_extra", C.c_int), ("step0", C.c_int)]
+                ("profile", C.c_int), ("mlp_extra", C.c_int), ("step0", C.c_int),
+                ("f64_gemm", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -84,6 +86,8 @@ _SIGS = {
     "chfsi_filter_batched": (C.c_int, [_P, C.c_int, _P]),
     "chfsi_filter_refine": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, _P, _P, C.c_double,
                                       C.c_double, C.c_double, _P]),
+    "chfsi_zgemm": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, _P, C.c_int,
+                              _P, C.c_int, C.c_double, _P, C.c_int, C.c_int]),
     "chfsi_orthonormalize": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_int, _P]),
     "chfsi_rayleigh_ritz": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, _P, _P]),
     "chfsi_residuals": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P, C.c_double, _P]),

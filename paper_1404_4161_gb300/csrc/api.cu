@@ -122,6 +122,8 @@ void validate_opts(const chfsi_opts& o) {
   CHFSI_REQUIRE(o.max_loops >= 1, "opts.max_loops");
   CHFSI_REQUIRE(o.switch_tol > 0.0, "opts.switch_tol");
   CHFSI_REQUIRE(o.mlp_extra >= 0 && o.step0 >= 0, "opts.mlp_extra/step0");
+  CHFSI_REQUIRE(o.f64_gemm == CHFSI_GEMM_FP64 || o.f64_gemm == CHFSI_GEMM_OZAKI,
+                "opts.f64_gemm");
 }
 
 inline double2* C2(double* p) { return reinterpret_cast<double2*>(p); }
@@ -273,6 +275,36 @@ void heevd(chfsi_ctx* ctx, int k, double2* G, double* w) {
                                       ")"};
 }
 
+// ------------------------------------------------ FP64 product engines ----
+bool use_oz(chfsi_ctx* ctx) { return ctx->opts.f64_gemm == CHFSI_GEMM_OZAKI; }
+
+// C = alpha A^H B + beta C
+void gemm_cn(chfsi_ctx* ctx, int K1, int K2, int Nr, const double2* A, int lda,
+             const double2* B, int ldb, double2* C, int ldc, double alpha = 1.0,
+             double beta = 0.0) {
+  if (use_oz(ctx))
+    oz_gemm_cn(ctx, K1, K2, Nr, A, lda, B, ldb, C, ldc, alpha, beta);
+  else
+    zgemm_cn(ctx, K1, K2, Nr, A, lda, B, ldb, C, ldc, alpha, beta);
+}
+
+// C = alpha A B + beta C (C may be the same buffer as the beta term only)
+void gemm_nn(chfsi_ctx* ctx, int M, int N, int K, const double2* A, int lda, const double2* B,
+             int ldb, double2* C, int ldc, double alpha = 1.0, double beta = 0.0) {
+  if (use_oz(ctx)) {
+    oz_gemm_nn(ctx, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta);
+    return;
+  }
+  EpiNN ep;
+  ep.alpha = alpha;
+  ep.beta = beta;
+  ep.P = beta != 0.0 ? C : nullptr;
+  ep.ldp = ldc;
+  ep.D = C;
+  ep.ldd = ldc;
+  zgemm_nn(ctx->stream, M, N, K, A, lda, B, ldb, ep);
+}
+
 // ------------------------------------------------- orthonormalisation ----
 // Alg. 1 line 6 on the device: two block Gram-Schmidt passes against the
 // locked block, column normalisation, then CholQR2 (a shifted Cholesky QR
@@ -283,15 +315,8 @@ void orthonormalize_dev(chfsi_ctx* ctx, int n, int nl, const double2* L, int k, 
   if (nl > 0) {
     double2* P = (double2*)ws_get(ctx, "qr_P", sizeof(double2) * (size_t)nl * k);
     for (int pass = 0; pass < 2; ++pass) {
-      zgemm_cn(ctx, nl, k, n, L, n, Y, n, P, nl);
-      EpiNN ep;
-      ep.alpha = -1.0;
-      ep.beta = 1.0;
-      ep.P = Y;
-      ep.ldp = n;
-      ep.D = Y;
-      ep.ldd = n;
-      zgemm_nn(st, n, k, nl, L, n, P, nl, ep);
+      gemm_cn(ctx, nl, k, n, L, n, Y, n, P, nl);
+      gemm_nn(ctx, n, k, nl, L, n, P, nl, Y, n, -1.0, 1.0);
     }
   }
   double* cn = (double*)ws_get(ctx, "qr_cn", sizeof(double) * k);
@@ -303,7 +328,7 @@ void orthonormalize_dev(chfsi_ctx* ctx, int n, int nl, const double2* L, int k, 
   int passes = 2;
   bool shifted = false;
   for (int pass = 0; pass < passes; ++pass) {
-    zgemm_cn(ctx, k, k, n, Y, n, Y, n, G, k);
+    gemm_cn(ctx, k, k, n, Y, n, Y, n, G, k);
     hermitianize(st, k, G, k);
     if (shifted && pass == 0) {
       cholqr_shift(st, n, k, G, k, shift);
@@ -321,10 +346,7 @@ void orthonormalize_dev(chfsi_ctx* ctx, int n, int nl, const double2* L, int k, 
                                              std::to_string(info) + ")"};
     }
     trtri_upper(ctx, k, G);
-    EpiNN ep;
-    ep.D = T;
-    ep.ldd = n;
-    zgemm_nn(st, n, k, k, Y, n, G, k, ep);
+    gemm_nn(ctx, n, k, k, Y, n, G, k, T, n);
     CHFSI_CUDA_TRY(cudaMemcpyAsync(Y, T, sizeof(double2) * (size_t)n * k,
                                    cudaMemcpyDeviceToDevice, st));
   }
@@ -332,34 +354,29 @@ void orthonormalize_dev(chfsi_ctx* ctx, int n, int nl, const double2* L, int k, 
 
 // ----------------------------------------------------- Rayleigh-Ritz ----
 void rayleigh_ritz_dev(chfsi_ctx* ctx, const double2* H, int n, int k, const double2* Q,
-                       double2* Y, double2* HY, double* evals) {
+                       double2* Y, double2* HY, double* evals, const std::string& hprefix = "",
+                       bool* h_sliced = nullptr) {
   cudaStream_t st = ctx->stream;
   double2* Z = (double2*)ws_get(ctx, "rr_Z", sizeof(double2) * (size_t)n * k);
   double2* G = (double2*)ws_get(ctx, "rr_G", sizeof(double2) * (size_t)k * k);
-  {
+  if (use_oz(ctx)) {
+    const bool fresh = !(h_sliced && *h_sliced);
+    oz_hemm(ctx, hprefix, H, n, Q, k, Z, fresh);
+    if (h_sliced) *h_sliced = true;
+  } else {
     EpiNN ep;
     ep.D = Z;
     ep.ldd = n;
     zgemm_nn(st, n, k, n, H, n, Q, n, ep);
   }
-  zgemm_cn(ctx, k, k, n, Q, n, Z, n, G, k);
+  gemm_cn(ctx, k, k, n, Q, n, Z, n, G, k);
   hermitianize(st, k, G, k);
   // The reduced eigensolver is iterative: never hand it NaN or Inf.
   if (any_nonfinite(ctx, (size_t)2 * k * k, (const double*)G))
     throw ChfsiError{CHFSI_ENAN, "NaN/Inf in the Rayleigh quotient"};
   heevd(ctx, k, G, evals);
-  {
-    EpiNN ep;
-    ep.D = Y;
-    ep.ldd = n;
-    zgemm_nn(st, n, k, k, Q, n, G, k, ep);
-  }
-  {
-    EpiNN ep;
-    ep.D = HY;
-    ep.ldd = n;
-    zgemm_nn(st, n, k, k, Z, n, G, k, ep);
-  }
+  gemm_nn(ctx, n, k, k, Q, n, G, k, Y, n);
+  gemm_nn(ctx, n, k, k, Z, n, G, k, HY, n);
 }
 
 // ------------------------------------------------- one problem's state --
@@ -395,6 +412,7 @@ struct Problem {
   cudaEvent_t ev[9] = {};
   double* psi = nullptr;  // refinement tables of the current loop
   double* fR = nullptr;
+  bool h_sliced = false;  // tensor-core slices of H built for this problem
 
   void* ws(const char* name, size_t bytes) { return ws_get(ctx, (pre + name).c_str(), bytes); }
   void mark(int i) { CHFSI_CUDA_TRY(cudaEventRecord(ev[i], st)); }
@@ -559,7 +577,7 @@ struct Problem {
     mark(3);
     orthonormalize_dev(ctx, n, nl, Lk, ka, Yf);
     mark(4);
-    rayleigh_ritz_dev(ctx, H, n, ka, Yf, Yrr, HY, lam);
+    rayleigh_ritz_dev(ctx, H, n, ka, Yf, Yrr, HY, lam, pre, &h_sliced);
     mark(5);
     residual_norms(st, n, ka, HY, Yrr, lam, norm_h, res);
     trace_finish(ctx, ka, res);
@@ -570,6 +588,12 @@ struct Problem {
     int* deg_h = (int*)(hp + 1024);
     CHFSI_CUDA_TRY(cudaMemcpyAsync(ctl_h, ctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, st));
     CHFSI_CUDA_TRY(cudaStreamSynchronize(st));
+    if (use_oz(ctx)) {
+      const int e = oz_check_error(ctx);
+      if (e)
+        throw ChfsiError{CHFSI_ETIMEOUT, "tensor-core GEMM: a bounded wait gave up (code " +
+                                             std::to_string(e) + ")"};
+    }
     if (ctl_h->nonfinite) throw ChfsiError{CHFSI_ENAN, "NaN/Inf in Ritz values or residuals"};
     const int n_new = ctl_h->n_new_locked;
     gather_columns(st, n, n_new, Yrr, n, lock_idx, Lk + (size_t)nl * n, n);
@@ -785,6 +809,7 @@ void chfsi_default_opts(chfsi_opts* o) {
   o->profile = 0;
   o->mlp_extra = 2;
   o->step0 = 0;
+  o->f64_gemm = CHFSI_GEMM_FP64;
 }
 
 const char* chfsi_strerror(int code) {
@@ -1089,6 +1114,40 @@ int chfsi_filter_refine(chfsi_ctx* ctx, const double* H, int n, int k, const dou
                                    ctx->stream));
     tc_filter_run_defect(ctx, C2(H), n, k, C2(Y), C2(R), ritz, degrees_host, dd, lam1, c, e,
                          C2(Yout));
+  });
+}
+
+int chfsi_zgemm(chfsi_ctx* ctx, int op_a, int m, int n, int k, double alpha, const double* A,
+                int lda, const double* B, int ldb, double beta, double* C, int ldc, int engine) {
+  if (!ctx) return CHFSI_EINVAL;
+  return run_guarded(ctx, [&] {
+    CHFSI_REQUIRE(m >= 0 && n >= 0 && k >= 0 && (op_a == 0 || op_a == 1), "bad zgemm shape");
+    if (m == 0 || n == 0) return;
+    CHFSI_REQUIRE(A && B && C, "bad zgemm buffers");
+    CHFSI_REQUIRE(engine == CHFSI_GEMM_FP64 || engine == CHFSI_GEMM_OZAKI, "bad engine");
+    if (engine == CHFSI_GEMM_OZAKI && !tc_filter_supported(ctx))
+      throw ChfsiError{CHFSI_ENOTSUP, "tensor-core GEMM needs an sm_103 device"};
+    const int saved = ctx->opts.f64_gemm;
+    ctx->opts.f64_gemm = engine;
+    try {
+      if (op_a == 1) {
+        CHFSI_REQUIRE(lda >= k && ldb >= k && ldc >= m, "bad leading dimensions");
+        gemm_cn(ctx, m, n, k, C2(A), lda, C2(B), ldb, C2(C), ldc, alpha, beta);
+      } else {
+        CHFSI_REQUIRE(lda >= m && ldb >= k && ldc >= m, "bad leading dimensions");
+        gemm_nn(ctx, m, n, k, C2(A), lda, C2(B), ldb, C2(C), ldc, alpha, beta);
+      }
+    } catch (...) {
+      ctx->opts.f64_gemm = saved;
+      throw;
+    }
+    ctx->opts.f64_gemm = saved;
+    if (engine == CHFSI_GEMM_OZAKI) {
+      const int e = oz_check_error(ctx);
+      if (e)
+        throw ChfsiError{CHFSI_ETIMEOUT, "tensor-core GEMM: a bounded wait gave up (code " +
+                                             std::to_string(e) + ")"};
+    }
   });
 }
 

@@ -225,6 +225,15 @@ void tc_filter_batched_release(chfsi_ctx* ctx);
 void residual_block(cudaStream_t st, int n, int k, const double2* HY, const double2* Y,
                     const double* lam, const int* perm, double2* R, double* lam_out);
 
+// FP64-accurate GEMMs on the tensor cores (gemm_ozaki.cu).
+void oz_hemm(chfsi_ctx* ctx, const std::string& prefix, const double2* H, int n,
+             const double2* Q, int k, double2* Z, bool reslice_h);
+void oz_gemm_cn(chfsi_ctx* ctx, int k1, int k2, int n, const double2* L, int ldl,
+                const double2* R, int ldr, double2* C, int ldc, double alpha, double beta);
+void oz_gemm_nn(chfsi_ctx* ctx, int m, int k2, int k1, const double2* S, int lds,
+                const double2* W, int ldw, double2* C, int ldc, double alpha, double beta);
+int oz_check_error(chfsi_ctx* ctx);
+
 // Degree MLP (mlp.cu).
 void mlp_create(chfsi_ctx* ctx);
 void mlp_destroy(chfsi_ctx* ctx);

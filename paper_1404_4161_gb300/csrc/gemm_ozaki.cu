@@ -1,0 +1,607 @@
+// FP64-accurate complex GEMM on the BF16 tensor cores (Ozaki scheme).
+//
+// GB300 issues FP64 on a narrow pipe (~1.1 TFLOP/s), while its BF16 tensor
+// cores run ~1.9 PFLOP/s.  This kernel computes the FP64 products of the
+// Rayleigh-Ritz step (Z = H Q, Alg. 1 line 7) to ~2^-43 accuracy with
+// error-free splitting (Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59,
+// 2012): every operand row (A) and column (B) is scaled by a power of two
+// to [-1, 1] and cut into S = 6 slices of 7-bit signed digits
+//     x / scale = sum_{p=1..6} d_p 2^{-7p},  |d_1| <= 128, |d_p| <= 64,
+// which BF16 represents exactly.  Digit products are exact (<= 2^14) and
+// the sum of the pairs with p + q = t over a K chunk of 512 stays within
+// 2^24 (t = 2: 512 * 2^14; t = 7: 512 * 8 * 2^12), so the FP32 tensor-core
+// accumulation of each group t = 2..7 (one TMEM accumulator each) is
+// exact.  Pairs with p + q > 7 are dropped: with the slicing remainder
+// (< 2^-43) they bound the error by ~2^-42 |scale_row| |scale_col| per
+// product.
+//
+// The complex product is the real GEMM of the filter kernels:
+// C (M x 2N) = A (M x 2K) * B (2K x 2N), A rows [Re S | Im S] of the left
+// factor, B columns interleaved (Re T_j ; -Im T_j), (Im T_j ; Re T_j).
+//
+// Kernel layout (one 128 x 64 output tile per CTA, 384 threads):
+//   warp 0 lane 0: TMA producer (6 A slices + 6 B slices per 32-wide K block)
+//   warp 1 lane 0: tcgen05.mma issuer (21 slice pairs per 16-wide K step)
+//   warp 2:        TMEM allocation (6 groups x 64 columns)
+//   warps 4-11:    epilogue: after every 512-wide K chunk, drain the six
+//                  group accumulators into double-float running sums (two
+//                  warps per TMEM lane quarter, one per half of the
+//                  columns); at the end scale back and store FP64.
+// Waits are bounded as in the filter kernels.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "tc_ptx.cuh"
+
+using namespace tcx;
+
+namespace {
+
+constexpr int OZ_S = 6;        // slices per operand
+constexpr int OZ_BETA = 7;     // bits per slice
+constexpr int OZ_BK = 32;      // K block (64-byte swizzle rows)
+constexpr int OZ_N = 64;       // tile columns (real)
+constexpr int OZ_KC = 512;     // exact-accumulation K chunk
+constexpr int OZ_GROUPS = 6;   // t = p + q = 2 .. 7
+constexpr int OZ_THREADS = 384;
+
+// Shared-memory descriptor, K-major, 64-byte swizzle: SBO = 8 rows x 64 B.
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
+         ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+// Error-free sum of two floats (Knuth): s + err = a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
+  s = a + b;
+  const float bp = s - a;
+  err = (a - (s - bp)) + (b - bp);
+}
+
+struct OzParams {
+  int M, N2, K2;       // rows, real columns (2 x complex), real K (2 x complex)
+  int kblocks;         // ceil(K2 / 32)
+  int kb_per_split;    // K blocks per split (multiple of 16 except the last)
+  int stages;
+  const double* sA;    // row scales (powers of two), M
+  const double* sB;    // column scales, N2
+  double2* C;          // output (complex, column-major, ldc) or partial buffer
+  int ldc;
+  size_t split_stride; // elements between split partials (0: no split)
+  int* err;
+};
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+oz_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
+               OzParams p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t a_slice = BM * OZ_BK * 2;     // 8 KB
+  const uint32_t b_slice = OZ_N * OZ_BK * 2;   // 4 KB
+  const uint32_t stage_bytes = OZ_S * (a_slice + b_slice);
+  uint64_t* bars = (uint64_t*)(smem + (size_t)p.stages * stage_bytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + p.stages;
+  uint64_t* accf = bars + 2 * p.stages;
+  uint64_t* acce = accf + 1;
+  uint32_t* tmem_slot = (uint32_t*)(acce + 1);
+  volatile int* abort_sh = (volatile int*)(tmem_slot + 1);
+  int* ep_count = (int*)(tmem_slot + 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM;
+  const int n0 = blockIdx.x * OZ_N;
+  const int kb0 = blockIdx.z * p.kb_per_split;
+  const int kb1 = min(p.kblocks, kb0 + p.kb_per_split);
+  const int nchunks = (kb1 - kb0 + OZ_KC / OZ_BK - 1) / (OZ_KC / OZ_BK);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    mbar_init(acce, 1);
+    *abort_sh = 0;
+    *ep_count = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 2) tmem_alloc(tmem_slot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    int issued = 0;
+    for (int kb = kb0, i = 0; kb < kb1; ++kb, ++i) {
+      const int s = i % p.stages;
+      const uint32_t ph = (uint32_t)(i / p.stages) & 1u;
+      if (!mbar_wait(&empty[s], ph ^ 1u, abort_sh, p.err, 11)) break;
+      unsigned char* st = smem + (size_t)s * stage_bytes;
+      mbar_arrive_expect_tx(&full[s], stage_bytes);
+      for (int sl = 0; sl < OZ_S; ++sl)
+        tma_load_3d(st + sl * a_slice, &mA, &full[s], kb * OZ_BK, m0, sl);
+      for (int sl = 0; sl < OZ_S; ++sl)
+        tma_load_3d(st + OZ_S * a_slice + sl * b_slice, &mB, &full[s], kb * OZ_BK, n0, sl);
+      issued = i + 1;
+    }
+    if (*abort_sh) {
+      for (int i = (issued > p.stages ? issued - p.stages : 0); i < issued; ++i) {
+        const unsigned long long t0 = globaltimer();
+        while (!mbar_try_wait(&full[i % p.stages], (uint32_t)(i / p.stages) & 1u) &&
+               globaltimer() - t0 < WAIT_NS) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = idesc_bf16(BM, OZ_N);
+    bool ok = true;
+    int i = 0;
+    for (int ch = 0; ch < nchunks && ok; ++ch) {
+      if (!mbar_wait(acce, ((uint32_t)ch & 1u) ^ 1u, abort_sh, p.err, 12)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const int kbc0 = kb0 + ch * (OZ_KC / OZ_BK);
+      const int kbc1 = min(kb1, kbc0 + OZ_KC / OZ_BK);
+      for (int kb = kbc0; kb < kbc1; ++kb, ++i) {
+        const int s = i % p.stages;
+        const uint32_t ph = (uint32_t)(i / p.stages) & 1u;
+        if (!mbar_wait(&full[s], ph, abort_sh, p.err, 13)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sa = smem_u32(smem + (size_t)s * stage_bytes);
+        const uint32_t sb = sa + OZ_S * a_slice;
+#pragma unroll
+        for (int kk = 0; kk < OZ_BK / 16; ++kk) {
+          const uint64_t adv = (uint64_t)((kk * 32) >> 4);
+          const bool first_k = (kb == kbc0) && (kk == 0);
+          uint32_t seen = 0;  // groups written in this K step
+#pragma unroll
+          for (int pa = 0; pa < OZ_S; ++pa) {
+#pragma unroll
+            for (int qb = 0; qb < OZ_S; ++qb) {
+              const int t = pa + qb;  // 0-based: p + q - 2
+              if (t > OZ_S - 1) continue;
+              const int g = t < OZ_GROUPS - 1 ? t : OZ_GROUPS - 1;
+              const uint32_t acc = (first_k && !(seen & (1u << g))) ? 0u : 1u;
+              seen |= 1u << g;
+              umma_bf16(tmem + (uint32_t)(g * OZ_N), desc_sw64(sa + pa * a_slice) + adv,
+                        desc_sw64(sb + qb * b_slice) + adv, idesc, acc);
+            }
+          }
+        }
+        umma_commit(&empty[s]);
+      }
+      if (!ok) break;
+      umma_commit(accf);
+    }
+  } else if (warp >= 4) {
+    // Epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, columns of half
+    // h = (w - 4) / 4; running sums in double-float (hi, lo).
+    const int q = warp & 3;
+    const int h = (warp - 4) >> 2;
+    const int row = m0 + q * 32 + lane;
+    const int c_begin = h * (OZ_N / 2);
+    float shi[OZ_N / 2], slo[OZ_N / 2];
+#pragma unroll
+    for (int c = 0; c < OZ_N / 2; ++c) {
+      shi[c] = 0.f;
+      slo[c] = 0.f;
+    }
+    const uint32_t tq = tmem + ((uint32_t)(q * 32) << 16);
+    bool ok = true;
+    for (int ch = 0; ch < nchunks; ++ch) {
+      if (!mbar_wait(accf, (uint32_t)ch & 1u, abort_sh, p.err, 14)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      // chunk value in units of 2^-14: sum_{g} 2^{-7 g} S_{g+2}, added into
+      // the (hi, lo) running sums group by group with error-free sums
+#pragma unroll
+      for (int g = 0; g < OZ_GROUPS; ++g) {
+        const float sc = ldexpf(1.f, -OZ_BETA * g);
+#pragma unroll
+        for (int cc = 0; cc < OZ_N / 2; cc += 16) {
+          float v[16];
+          __syncwarp();
+          tmem_ld16(tq + (uint32_t)(g * OZ_N + c_begin + cc), v);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            float s2, e2;
+            two_sum(shi[cc + c], v[c] * sc, s2, e2);
+            shi[cc + c] = s2;
+            slo[cc + c] += e2;
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < OZ_N / 2; ++c) {  // renormalise
+        const float t2 = shi[c] + slo[c];
+        slo[c] = slo[c] - (t2 - shi[c]);
+        shi[c] = t2;
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        __threadfence_block();
+        const int arrived = atomicAdd(ep_count, 1);
+        if (arrived == 8 * ch + 7) mbar_arrive(acce);
+      }
+    }
+    if (ok && row < p.M) {
+      const double rs = p.sA[row] * 6.103515625e-05;  // 2^-14
+#pragma unroll
+      for (int c = 0; c < OZ_N / 2; c += 2) {
+        const int gc = n0 + c_begin + c;  // even real column = real part
+        if (gc >= p.N2) break;
+        const int j = gc >> 1;
+        const double re = ((double)shi[c] + (double)slo[c]) * rs * p.sB[gc];
+        const double im = ((double)shi[c + 1] + (double)slo[c + 1]) * rs * p.sB[gc + 1];
+        double2* out = p.C + blockIdx.z * p.split_stride + (size_t)row + (size_t)j * p.ldc;
+        *out = make_double2(re, im);
+      }
+    }
+    tc_fence_before();
+  }
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// ---- operand slicing ------------------------------------------------------
+__device__ __forceinline__ double pow2_scale(double amax) {
+  if (!(amax > 0.0)) return 1.0;
+  int e;
+  frexp(amax, &e);  // amax = f 2^e, f in [0.5, 1)
+  return ldexp(1.0, e);  // > amax
+}
+
+__device__ __forceinline__ void slice_value(double v, __nv_bfloat16* out, size_t stride) {
+  double r = v;
+#pragma unroll
+  for (int sl = 0; sl < OZ_S; ++sl) {
+    const double sc = ldexp(1.0, OZ_BETA * (sl + 1));
+    const double d = rint(r * sc);
+    r -= d / sc;
+    out[(size_t)sl * stride] = __double2bfloat16(d);
+  }
+}
+
+template <int NT>
+__device__ double block_max(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < NT / 32 ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) sh[0] = v;
+  }
+  __syncthreads();
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// A rows from conjugated columns of S (rows x cols, column-major, lds):
+// row i = [Re S[:, i] | -Im S[:, i]]  (for Hermitian H this is row i of H;
+// for S = Q it is row i of Q^H).  With mu (device scalar) the diagonal
+// entry S[i, i] is taken as S[i, i] - mu.  Slices: [sl][i][x], pitch P.
+__global__ void __launch_bounds__(256)
+oz_slice_a_conjcols_kernel(int rows, int lds, const double2* __restrict__ S, int P,
+                           __nv_bfloat16* __restrict__ out, size_t slice_stride,
+                           double* __restrict__ scale, const double* __restrict__ mu) {
+  __shared__ double sh[8];
+  const int i = blockIdx.x;
+  const double2* col = S + (size_t)i * lds;
+  const double shift = mu ? *mu : 0.0;
+  double m = 0.0;
+  for (int x = threadIdx.x; x < rows; x += 256) {
+    const double re = col[x].x - (x == i ? shift : 0.0);
+    m = fmax(m, fmax(fabs(re), fabs(col[x].y)));
+  }
+  const double sc = pow2_scale(block_max<256>(m, sh));
+  if (threadIdx.x == 0) scale[i] = sc;
+  const double inv = 1.0 / sc;
+  __nv_bfloat16* o = out + (size_t)i * P;
+  for (int x = threadIdx.x; x < rows; x += 256) {
+    const double re = col[x].x - (x == i ? shift : 0.0);
+    slice_value(re * inv, o + x, slice_stride);
+    slice_value(-col[x].y * inv, o + rows + x, slice_stride);
+  }
+}
+
+// mu = mean of Re diag(H) (one block).
+__global__ void __launch_bounds__(256) oz_diag_mean_kernel(int n, const double2* H, double* mu) {
+  __shared__ double sh[8];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) s += H[(size_t)i * n + i].x;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += sh[w];
+    *mu = t / n;
+  }
+}
+
+// C += mu Q (n x k, both column-major)
+__global__ void oz_add_shift_kernel(int n, int k, const double* mu, const double2* Q,
+                                    double2* C) {
+  const size_t total = (size_t)n * k;
+  const double m = *mu;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const double2 q = Q[t];
+    double2 c = C[t];
+    c.x = fma(m, q.x, c.x);
+    c.y = fma(m, q.y, c.y);
+    C[t] = c;
+  }
+}
+
+// A rows from rows of S (rows x cols, column-major, lds): row r =
+// [Re S[r, :] | Im S[r, :]].  One block per row (strided reads; S is
+// n x k with small k).
+__global__ void __launch_bounds__(256)
+oz_slice_a_rows_kernel(int cols, int lds, const double2* __restrict__ S, int P,
+                       __nv_bfloat16* __restrict__ out, size_t slice_stride,
+                       double* __restrict__ scale) {
+  __shared__ double sh[8];
+  const int r = blockIdx.x;
+  double m = 0.0;
+  for (int x = threadIdx.x; x < cols; x += 256) {
+    const double2 v = S[(size_t)r + (size_t)x * lds];
+    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+  }
+  const double sc = pow2_scale(block_max<256>(m, sh));
+  if (threadIdx.x == 0) scale[r] = sc;
+  const double inv = 1.0 / sc;
+  __nv_bfloat16* o = out + (size_t)r * P;
+  for (int x = threadIdx.x; x < cols; x += 256) {
+    const double2 v = S[(size_t)r + (size_t)x * lds];
+    slice_value(v.x * inv, o + x, slice_stride);
+    slice_value(v.y * inv, o + cols + x, slice_stride);
+  }
+}
+
+// B from T (rows x cols complex, column-major, ldt): real column 2j =
+// (Re T_j ; -Im T_j), 2j + 1 = (Im T_j ; Re T_j); stored K-major (row 2j of
+// B^T), slices [sl][2j][x], pitch P; scale per real column (same for the
+// pair).
+__global__ void __launch_bounds__(256)
+oz_slice_b_kernel(int rows, int ldt, const double2* __restrict__ T, int P,
+                  __nv_bfloat16* __restrict__ out, size_t slice_stride,
+                  double* __restrict__ scale) {
+  __shared__ double sh[8];
+  const int j = blockIdx.x;
+  const double2* col = T + (size_t)j * ldt;
+  double m = 0.0;
+  for (int x = threadIdx.x; x < rows; x += 256) m = fmax(m, fmax(fabs(col[x].x), fabs(col[x].y)));
+  const double sc = pow2_scale(block_max<256>(m, sh));
+  if (threadIdx.x == 0) {
+    scale[2 * j] = sc;
+    scale[2 * j + 1] = sc;
+  }
+  const double inv = 1.0 / sc;
+  __nv_bfloat16* o0 = out + (size_t)(2 * j) * P;
+  __nv_bfloat16* o1 = o0 + P;
+  for (int x = threadIdx.x; x < rows; x += 256) {
+    const double re = col[x].x * inv, im = col[x].y * inv;
+    slice_value(re, o0 + x, slice_stride);
+    slice_value(-im, o0 + rows + x, slice_stride);
+    slice_value(im, o1 + x, slice_stride);
+    slice_value(re, o1 + rows + x, slice_stride);
+  }
+}
+
+__global__ void oz_reduce_kernel(int M, int Nc, int splits, const double2* part,
+                                 size_t split_stride, int ldp, double2* C, int ldc,
+                                 double alpha, double beta) {
+  const size_t total = (size_t)M * Nc;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % M), j = (int)(t / M);
+    double2 s = make_double2(0.0, 0.0);
+    for (int z = 0; z < splits; ++z) {
+      const double2 v = part[z * split_stride + i + (size_t)j * ldp];
+      s.x += v.x;
+      s.y += v.y;
+    }
+    double2* c = C + i + (size_t)j * ldc;
+    double2 o = make_double2(alpha * s.x, alpha * s.y);
+    if (beta != 0.0) {
+      o.x = fma(beta, c->x, o.x);
+      o.y = fma(beta, c->y, o.y);
+    }
+    *c = o;
+  }
+}
+
+CUtensorMap make_map3(const void* base, int inner, int rows, int P, int slices, int box_inner,
+                      int box_rows, size_t slice_stride_elems) {
+  CUtensorMap m;
+  const cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)rows, (cuuint64_t)slices};
+  const cuuint64_t strides[2] = {(cuuint64_t)P * 2, (cuuint64_t)slice_stride_elems * 2};
+  const cuuint32_t box[3] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = get_encode()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base),
+                            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    throw ChfsiError{CHFSI_ECUDA, "cuTensorMapEncodeTiled (3d) failed (" + std::to_string((int)r) + ")"};
+  return m;
+}
+
+}  // namespace
+
+// Sliced operand storage and the launch.
+struct OzOperand {
+  __nv_bfloat16* data = nullptr;  // OZ_S slices
+  double* scale = nullptr;
+  int rows = 0;      // M (A) or 2N (B)
+  int K2 = 0;        // real K
+  int P = 0;         // pitch (elements)
+  size_t stride = 0; // elements per slice
+};
+
+static void oz_alloc(chfsi_ctx* ctx, const std::string& name, OzOperand& o, int rows, int K2) {
+  o.rows = rows;
+  o.K2 = K2;
+  o.P = (K2 + 7) / 8 * 8;
+  o.stride = (size_t)rows * o.P;
+  o.data = (__nv_bfloat16*)ws_get(ctx, (name + ".sl").c_str(),
+                                  sizeof(__nv_bfloat16) * OZ_S * o.stride + 256);
+  o.scale = (double*)ws_get(ctx, (name + ".sc").c_str(), sizeof(double) * (rows + 8));
+}
+
+// C (M x Nc complex) = alpha * left * right + beta * C, where the left factor
+// is given as A rows (already sliced) and the right factor as B (sliced).
+static void oz_run(chfsi_ctx* ctx, const OzOperand& A, const OzOperand& B, double2* C, int ldc,
+                   double alpha, double beta) {
+  cudaStream_t st = ctx->stream;
+  const int M = A.rows, N2 = B.rows, K2 = A.K2;
+  const int kblocks = (K2 + OZ_BK - 1) / OZ_BK;
+  const int mt = (M + BM - 1) / BM, nt = (N2 + OZ_N - 1) / OZ_N;
+  const int tiles = mt * nt;
+  // split K (in whole 512-chunks) when the tiles do not fill the GPU
+  int splits = 1;
+  const int chunks = (kblocks + OZ_KC / OZ_BK - 1) / (OZ_KC / OZ_BK);
+  while (tiles * splits * 2 <= ctx->sm_count && splits * 2 <= chunks) splits *= 2;
+  const int chunks_per = (chunks + splits - 1) / splits;
+  const int kb_per = chunks_per * (OZ_KC / OZ_BK);
+  splits = (kblocks + kb_per - 1) / kb_per;
+  const uint32_t stage_bytes = OZ_S * (BM * OZ_BK * 2 + OZ_N * OZ_BK * 2);
+  int stages = (int)((220u * 1024u) / stage_bytes);
+  stages = std::max(2, std::min(stages, 4));
+  const size_t smem = 1024 + (size_t)stages * stage_bytes + 8 * (2 * stages + 2) + 32;
+  static bool attr = false;
+  if (!attr) {
+    CHFSI_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr = true;
+  }
+  CUtensorMap mA = make_map3(A.data, K2, M, A.P, OZ_S, OZ_BK, BM, A.stride);
+  CUtensorMap mB = make_map3(B.data, K2, N2, B.P, OZ_S, OZ_BK, OZ_N, B.stride);
+  int* err = (int*)ws_get(ctx, "oz_err", sizeof(int));
+  CHFSI_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+  const int Nc = N2 / 2;
+  OzParams p;
+  p.M = M;
+  p.N2 = N2;
+  p.K2 = K2;
+  p.kblocks = kblocks;
+  p.kb_per_split = kb_per;
+  p.stages = stages;
+  p.sA = A.scale;
+  p.sB = B.scale;
+  p.err = err;
+  const bool direct = splits == 1 && alpha == 1.0 && beta == 0.0;
+  double2* part = nullptr;
+  if (direct) {
+    p.C = C;
+    p.ldc = ldc;
+    p.split_stride = 0;
+  } else {
+    part = (double2*)ws_get(ctx, "oz_part", sizeof(double2) * (size_t)splits * M * Nc);
+    p.C = part;
+    p.ldc = M;
+    p.split_stride = (size_t)M * Nc;
+  }
+  dim3 grid(nt, mt, splits);
+  const int slot = kt_begin(st);
+  oz_gemm_kernel<<<grid, OZ_THREADS, smem, st>>>(mA, mB, p);
+  chfsi_check_launch("oz_gemm");
+  kt_end(st, slot, KT_F64, 8.0 * (double)M * Nc * (K2 / 2));
+  if (!direct) {
+    const size_t total = (size_t)M * Nc;
+    oz_reduce_kernel<<<(unsigned)std::min<size_t>((total + 255) / 256, 4096), 256, 0, st>>>(
+        M, Nc, splits, part, (size_t)M * Nc, M, C, ldc, alpha, beta);
+    chfsi_check_launch("oz_reduce");
+  }
+}
+
+int oz_check_error(chfsi_ctx* ctx) {
+  int* h = (int*)pinned_get(ctx, 64);
+  CHFSI_CUDA_TRY(cudaMemcpyAsync(h, ws_get(ctx, "oz_err", sizeof(int)), sizeof(int),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+  CHFSI_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return *h;
+}
+
+// Z (n x k) = H Q with H Hermitian n x n, both complex column-major,
+// computed as (H - mu I) Q + mu Q with mu = mean(Re diag H): the diagonal of
+// a dense Hermitian matrix is often far larger than its other entries and
+// would otherwise set each row's scale.  The sliced H - mu I is kept in the
+// workspace named after `prefix` and rebuilt when reslice_h is set.
+void oz_hemm(chfsi_ctx* ctx, const std::string& prefix, const double2* H, int n,
+             const double2* Q, int k, double2* Z, bool reslice_h) {
+  OzOperand A, B;
+  oz_alloc(ctx, prefix + "ozH", A, n, 2 * n);
+  double* mu = (double*)ws_get(ctx, (prefix + "ozH.mu").c_str(), sizeof(double));
+  if (reslice_h) {
+    oz_diag_mean_kernel<<<1, 256, 0, ctx->stream>>>(n, H, mu);
+    chfsi_check_launch("oz_diag_mean");
+    oz_slice_a_conjcols_kernel<<<n, 256, 0, ctx->stream>>>(n, n, H, A.P, A.data, A.stride,
+                                                           A.scale, mu);
+    chfsi_check_launch("oz_slice_h");
+  }
+  oz_alloc(ctx, "ozQ", B, 2 * k, 2 * n);
+  oz_slice_b_kernel<<<k, 256, 0, ctx->stream>>>(n, n, Q, B.P, B.data, B.stride, B.scale);
+  chfsi_check_launch("oz_slice_b");
+  oz_run(ctx, A, B, Z, n, 1.0, 0.0);
+  const size_t total = (size_t)n * k;
+  oz_add_shift_kernel<<<(unsigned)std::min<size_t>((total + 255) / 256, 4096), 256, 0,
+                        ctx->stream>>>(n, k, mu, Q, Z);
+  chfsi_check_launch("oz_add_shift");
+}
+
+// C (k1 x k2) = alpha * L^H R + beta * C with L n x k1, R n x k2.
+void oz_gemm_cn(chfsi_ctx* ctx, int k1, int k2, int n, const double2* L, int ldl,
+                const double2* R, int ldr, double2* C, int ldc, double alpha, double beta) {
+  OzOperand A, B;
+  oz_alloc(ctx, "ozL", A, k1, 2 * n);
+  oz_slice_a_conjcols_kernel<<<k1, 256, 0, ctx->stream>>>(n, ldl, L, A.P, A.data, A.stride,
+                                                          A.scale, nullptr);
+  chfsi_check_launch("oz_slice_l");
+  oz_alloc(ctx, "ozR", B, 2 * k2, 2 * n);
+  oz_slice_b_kernel<<<k2, 256, 0, ctx->stream>>>(n, ldr, R, B.P, B.data, B.stride, B.scale);
+  chfsi_check_launch("oz_slice_r");
+  oz_run(ctx, A, B, C, ldc, alpha, beta);
+}
+
+// C (m x k2) = alpha * S W + beta * C with S m x k1 (lds), W k1 x k2 (ldw).
+void oz_gemm_nn(chfsi_ctx* ctx, int m, int k2, int k1, const double2* S, int lds,
+                const double2* W, int ldw, double2* C, int ldc, double alpha, double beta) {
+  OzOperand A, B;
+  oz_alloc(ctx, "ozS", A, m, 2 * k1);
+  oz_slice_a_rows_kernel<<<m, 256, 0, ctx->stream>>>(k1, lds, S, A.P, A.data, A.stride,
+                                                     A.scale);
+  chfsi_check_launch("oz_slice_s");
+  oz_alloc(ctx, "ozW", B, 2 * k2, 2 * k1);
+  oz_slice_b_kernel<<<k2, 256, 0, ctx->stream>>>(k1, ldw, W, B.P, B.data, B.stride, B.scale);
+  chfsi_check_launch("oz_slice_w");
+  oz_run(ctx, A, B, C, ldc, alpha, beta);
+}

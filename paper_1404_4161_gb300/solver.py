@@ -159,6 +159,15 @@ class Chfsi:
                                                  _ptr(out)))
         return out
 
+    def zgemm(self, op_a, A_cm, B_cm, m, n, k, alpha=1.0, beta=0.0, C_cm=None, engine=L.GEMM_OZAKI):
+        """Column-major operands as colmajor() tensors: A_cm (cols, rows) etc."""
+        if C_cm is None:
+            C_cm = torch.zeros((n, m), dtype=torch.complex128, device=A_cm.device)
+        self._check(self.lib.chfsi_zgemm(self.ctx, op_a, m, n, k, alpha, _ptr(A_cm),
+                                         A_cm.shape[1], _ptr(B_cm), B_cm.shape[1], beta,
+                                         _ptr(C_cm), C_cm.shape[1], engine))
+        return C_cm
+
     def orthonormalize(self, Yc, Lc=None):
         k, n = Yc.shape
         nl = 0 if Lc is None else Lc.shape[0]
