@@ -458,6 +458,8 @@ def main():
             "loops": [x["loops"] for x in last],
             "phase_ms": {p: sum(x["ms_" + p] for x in last)
                          for p in ["lanczos", "filter", "qr", "rr", "resid", "lock"]},
+            "kernel_ms": {"fp64_products": k64_ms, "tc_filter": ktc_ms,
+                          "cusolver_kxk": sum(x["k_solver_ms"] for x in last)},
             "roofline": roof,
             "filter_roofline": tc_roof,
             "fp64_gemm_roofline": f64_roof,

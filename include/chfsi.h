@@ -59,8 +59,8 @@ extern "C" {
 /* Engine of the FP64 products (H Q, Gram matrices, block products). */
 #define CHFSI_GEMM_FP64 0   /* DFMA kernels on the FP64 pipe                 */
 #define CHFSI_GEMM_OZAKI 1  /* FP64-accurate emulation on the BF16 tensor    */
-                            /* cores: 6 x 7-bit error-free slices, 21 slice  */
-                            /* products, exact FP32 chunk sums (~2^-42 of    */
+                            /* cores: 7 x 7-bit error-free slices, 28 slice  */
+                            /* products, exact FP32 chunk sums (~2^-48 of    */
                             /* row scale x column scale per product)         */
 
 /* Degree model (Alg. 1 line 11). */
@@ -113,6 +113,8 @@ typedef struct chfsi_stats {
   double k_tc_ms;           /* tcgen05 filter-step kernel                */
   double k_tc_flops;        /* its useful complex flops, 8 n^2 k_active  */
   long long k_tc_launches;
+  double k_solver_ms;       /* cuSOLVER k x k Cholesky / inverse / eigh  */
+  long long k_solver_calls;
   int loops_mlp;            /* loops whose degrees came from the MLP     */
   int mlp_fallback;         /* 1 if the MLP stalled and the analytic rule */
                             /* took over for the rest of this problem     */

@@ -40,6 +40,7 @@ class Stats(C.Structure):
                 ("launches", C.c_longlong), ("k_f64_ms", C.c_double), ("k_f64_flops", C.c_double),
                 ("k_f64_launches", C.c_longlong), ("k_tc_ms", C.c_double),
                 ("k_tc_flops", C.c_double), ("k_tc_launches", C.c_longlong),
+                ("k_solver_ms", C.c_double), ("k_solver_calls", C.c_longlong),
                 ("loops_mlp", C.c_int), ("mlp_fallback", C.c_int)]
 
     def as_dict(self):

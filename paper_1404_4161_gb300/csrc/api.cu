@@ -235,9 +235,11 @@ int potrf_upper(chfsi_ctx* ctx, int k, double2* G) {
   CHFSI_SOLVER_TRY(cusolverDnZpotrf_bufferSize(ctx->solver, CUBLAS_FILL_MODE_UPPER, k,
                                                (cuDoubleComplex*)G, k, &lwork));
   void* work = ws_get(ctx, "potrf_work", sizeof(cuDoubleComplex) * (size_t)std::max(lwork, 1));
+  const int slot = kt_begin(ctx->stream);
   CHFSI_SOLVER_TRY(cusolverDnZpotrf(ctx->solver, CUBLAS_FILL_MODE_UPPER, k,
                                     (cuDoubleComplex*)G, k, (cuDoubleComplex*)work, lwork,
                                     dev_info(ctx)));
+  kt_end(ctx->stream, slot, KT_SOLVER, 0.0);
   return read_info(ctx);
 }
 
@@ -250,9 +252,11 @@ void trtri_upper(chfsi_ctx* ctx, int k, double2* R) {
                                                &dbytes, &hbytes));
   void* dwork = ws_get(ctx, "trtri_work", std::max<size_t>(dbytes, 16));
   std::vector<char> hwork(std::max<size_t>(hbytes, 16));
+  const int slot = kt_begin(ctx->stream);
   CHFSI_SOLVER_TRY(cusolverDnXtrtri(ctx->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT,
                                     k, CUDA_C_64F, R, k, dwork, dbytes, hwork.data(), hbytes,
                                     dev_info(ctx)));
+  kt_end(ctx->stream, slot, KT_SOLVER, 0.0);
   const int info = read_info(ctx);
   if (info != 0)
     throw ChfsiError{CHFSI_EBREAKDOWN, "triangular inverse: singular R (info " +
@@ -266,9 +270,11 @@ void heevd(chfsi_ctx* ctx, int k, double2* G, double* w) {
                                                CUBLAS_FILL_MODE_LOWER, k, (cuDoubleComplex*)G,
                                                k, w, &lwork));
   void* work = ws_get(ctx, "heevd_work", sizeof(cuDoubleComplex) * (size_t)std::max(lwork, 1));
+  const int slot = kt_begin(ctx->stream);
   CHFSI_SOLVER_TRY(cusolverDnZheevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR,
                                     CUBLAS_FILL_MODE_LOWER, k, (cuDoubleComplex*)G, k, w,
                                     (cuDoubleComplex*)work, lwork, dev_info(ctx)));
+  kt_end(ctx->stream, slot, KT_SOLVER, 0.0);
   const int info = read_info(ctx);
   if (info != 0)
     throw ChfsiError{CHFSI_ECUDA, "reduced eigensolve failed (info " + std::to_string(info) +
@@ -309,7 +315,8 @@ void gemm_nn(chfsi_ctx* ctx, int M, int N, int K, const double2* A, int lda, con
 // Alg. 1 line 6 on the device: two block Gram-Schmidt passes against the
 // locked block, column normalisation, then CholQR2 (a shifted Cholesky QR
 // pass first when the Gram matrix is not numerically positive definite).
-void orthonormalize_dev(chfsi_ctx* ctx, int n, int nl, const double2* L, int k, double2* Y) {
+void orthonormalize_dev(chfsi_ctx* ctx, int n, int nl, const double2* L, int k, double2* Y,
+                        bool adaptive = false) {
   cudaStream_t st = ctx->stream;
   if (k <= 0) return;
   if (nl > 0) {
@@ -349,6 +356,20 @@ void orthonormalize_dev(chfsi_ctx* ctx, int n, int nl, const double2* L, int k, 
     gemm_nn(ctx, n, k, k, Y, n, G, k, T, n);
     CHFSI_CUDA_TRY(cudaMemcpyAsync(Y, T, sizeof(double2) * (size_t)n * k,
                                    cudaMemcpyDeviceToDevice, st));
+    if (adaptive && pass == passes - 2) {
+      // Before the last pass: when the block is already orthonormal to
+      // 1e-8, one Newton-Schulz step Y (3I - Y^H Y)/2 leaves it orthonormal
+      // to the Gram's accuracy (error ~ the square of 1e-8) and replaces the
+      // last Cholesky pass.
+      gemm_cn(ctx, k, k, n, Y, n, Y, n, G, k);
+      if (deviation_from_identity(ctx, k, G) <= 1e-8) {
+        ns_matrix(st, k, G, G);
+        gemm_nn(ctx, n, k, k, Y, n, G, k, T, n);
+        CHFSI_CUDA_TRY(cudaMemcpyAsync(Y, T, sizeof(double2) * (size_t)n * k,
+                                       cudaMemcpyDeviceToDevice, st));
+        break;
+      }
+    }
   }
 }
 
@@ -374,7 +395,10 @@ void rayleigh_ritz_dev(chfsi_ctx* ctx, const double2* H, int n, int k, const dou
   // The reduced eigensolver is iterative: never hand it NaN or Inf.
   if (any_nonfinite(ctx, (size_t)2 * k * k, (const double*)G))
     throw ChfsiError{CHFSI_ENAN, "NaN/Inf in the Rayleigh quotient"};
-  heevd(ctx, k, G, evals);
+  if (use_oz(ctx))
+    reduced_eigh_mixed(ctx, k, G, evals);
+  else
+    heevd(ctx, k, G, evals);
   gemm_nn(ctx, n, k, k, Q, n, G, k, Y, n);
   gemm_nn(ctx, n, k, k, Z, n, G, k, HY, n);
 }
@@ -575,7 +599,7 @@ struct Problem {
     S.col_degrees += sdeg;
     S.filter_launches += chfsi_launch_counter() - fl0;
     mark(3);
-    orthonormalize_dev(ctx, n, nl, Lk, ka, Yf);
+    orthonormalize_dev(ctx, n, nl, Lk, ka, Yf, use_oz(ctx));
     mark(4);
     rayleigh_ritz_dev(ctx, H, n, ka, Yf, Yrr, HY, lam, pre, &h_sliced);
     mark(5);
@@ -678,6 +702,8 @@ void copy_kernel_times(chfsi_stats& S, const KernelTimer& t) {
   S.k_tc_ms = t.ms[KT_TC];
   S.k_tc_flops = t.fl[KT_TC];
   S.k_tc_launches = t.n[KT_TC];
+  S.k_solver_ms = t.ms[KT_SOLVER];
+  S.k_solver_calls = t.n[KT_SOLVER];
 }
 
 struct TimerScope {

@@ -46,15 +46,15 @@ struct ChfsiError {
 // timer is installed for the calling thread (solver with opts.profile),
 // kt_begin / kt_end bracket a launch with CUDA events on its stream and
 // kt_resolve adds the elapsed times after the stream has been synchronised.
-enum KtCat { KT_F64 = 0, KT_TC = 1, KT_NCAT = 2 };
+enum KtCat { KT_F64 = 0, KT_TC = 1, KT_SOLVER = 2, KT_NCAT = 3 };
 struct KernelTimer {
   std::vector<cudaEvent_t> ev;
   std::vector<int> cat;
   std::vector<double> flops;
   int used = 0;
-  double ms[KT_NCAT] = {0, 0};
-  double fl[KT_NCAT] = {0, 0};
-  long long n[KT_NCAT] = {0, 0};
+  double ms[KT_NCAT] = {0, 0, 0};
+  double fl[KT_NCAT] = {0, 0, 0};
+  long long n[KT_NCAT] = {0, 0, 0};
 };
 KernelTimer* kt_current();
 void kt_install(KernelTimer* t);
@@ -156,6 +156,9 @@ void copy_columns(cudaStream_t st, int n, int k, const double2* src, int lds, do
 // Shift for shifted CholQR from trace(G) (Fukaya et al., SISC 2020).
 void cholqr_shift(cudaStream_t st, int n, int k, const double2* G, int ldg, double* shift);
 int any_nonfinite(chfsi_ctx* ctx, size_t count, const double* v);
+// max |G - I| (synchronises) and T = (3I - G)/2 for a Newton-Schulz step.
+double deviation_from_identity(chfsi_ctx* ctx, int k, const double2* G);
+void ns_matrix(cudaStream_t st, int k, const double2* G, double2* T);
 
 // Lanczos helpers.
 void lanczos_start_vec(cudaStream_t st, int n, unsigned long long seed, double2* v);
@@ -228,11 +231,18 @@ void residual_block(cudaStream_t st, int n, int k, const double2* HY, const doub
 // FP64-accurate GEMMs on the tensor cores (gemm_ozaki.cu).
 void oz_hemm(chfsi_ctx* ctx, const std::string& prefix, const double2* H, int n,
              const double2* Q, int k, double2* Z, bool reslice_h);
+// ns = slices per operand: 6 (~2^-41 of the row x column scales), 7
+// (~2^-48) or 8 (~2^-55)
 void oz_gemm_cn(chfsi_ctx* ctx, int k1, int k2, int n, const double2* L, int ldl,
-                const double2* R, int ldr, double2* C, int ldc, double alpha, double beta);
+                const double2* R, int ldr, double2* C, int ldc, double alpha, double beta,
+                int ns = 7);
 void oz_gemm_nn(chfsi_ctx* ctx, int m, int k2, int k1, const double2* S, int lds,
-                const double2* W, int ldw, double2* C, int ldc, double alpha, double beta);
+                const double2* W, int ldw, double2* C, int ldc, double alpha, double beta,
+                int ns = 7);
 int oz_check_error(chfsi_ctx* ctx);
+// Reduced Hermitian eigensolve: FP32 eigenpairs refined to FP64 accuracy
+// (eig_mixed.cu); eigenvectors overwrite G, eigenvalues ascending in w.
+void reduced_eigh_mixed(chfsi_ctx* ctx, int k, double2* G, double* w);
 
 // Degree MLP (mlp.cu).
 void mlp_create(chfsi_ctx* ctx);

@@ -351,11 +351,13 @@ __device__ int sturm_count(int m, const double* a, const double* b, double x) {
   return cnt;
 }
 
-// Extreme eigenvalues of the Lanczos tridiagonal by bisection on Sturm
-// counts; out4 = {theta_max + beta_m, theta_min, theta_max, max|theta|},
-// beta_m the norm of the last residual vector.
+// Extreme eigenvalues of the Lanczos tridiagonal by multisection on Sturm
+// counts: one warp, each round splits the bracket into 33 parts and keeps
+// the part holding the wanted eigenvalue (5 bits per round instead of 1).
+// out4 = {theta_max + beta_m, theta_min, theta_max, max|theta|}, beta_m the
+// norm of the last residual vector.
 __global__ void tridiag_bounds_kernel(int m_in, const double* a, const double* b, double* out) {
-  if (threadIdx.x != 0) return;
+  const int lane = threadIdx.x & 31;
   // Steps after an (almost) invariant Krylov space are not used: the
   // recurrence stops at the first beta_j <= 1e-14 max(|alpha_j|, 1).
   int m = m_in;
@@ -369,19 +371,30 @@ __global__ void tridiag_bounds_kernel(int m_in, const double* a, const double* b
   }
   double th[2];
   for (int which = 0; which < 2; ++which) {
-    const int target = which == 0 ? 1 : m;  // count below x >= target
+    const int target = which == 0 ? 1 : m;  // smallest x with count(x) >= target
     double l = lo - 1e-12 * fabs(lo) - 1e-300, h = hi + 1e-12 * fabs(hi) + 1e-300;
-    for (int it = 0; it < 200; ++it) {
-      const double mid = 0.5 * (l + h);
-      if (mid <= l || mid >= h) break;
-      if (sturm_count(m, a, b, mid) >= target) h = mid; else l = mid;
+    for (int it = 0; it < 40; ++it) {
+      const double step = (h - l) / 33.0;
+      const double x = l + step * (lane + 1);
+      const bool ge = sturm_count(m, a, b, x) >= target;
+      const unsigned mask = __ballot_sync(0xffffffffu, ge);
+      // first lane whose point has count >= target: new bracket (x_{f-1}, x_f]
+      const int f = mask ? __ffs(mask) - 1 : 32;
+      const double nl = l + step * f;
+      const double nh = (f < 32) ? l + step * (f + 1) : h;
+      if (!(nl < nh) || (nl == l && nh == h)) break;
+      l = nl;
+      h = nh;
+      if (h - l <= 4e-16 * fmax(fabs(l), fabs(h))) break;
     }
     th[which] = 0.5 * (l + h);
   }
-  out[1] = th[0];
-  out[2] = th[1];
-  out[0] = th[1] + b[m - 1];
-  out[3] = fmax(fabs(th[0]), fabs(th[1]));
+  if (lane == 0) {
+    out[1] = th[0];
+    out[2] = th[1];
+    out[0] = th[1] + b[m - 1];
+    out[3] = fmax(fabs(th[0]), fabs(th[1]));
+  }
 }
 
 __global__ void residual_block_kernel(int n, const double2* __restrict__ HY,
@@ -552,4 +565,65 @@ void residual_block(cudaStream_t st, int n, int k, const double2* HY, const doub
   residual_block_kernel<<<dim3(grid_for(n, 256, 64), k), 256, 0, st>>>(n, HY, Y, lam, perm, R,
                                                                         lam_out);
   chfsi_check_launch("residual_block");
+}
+
+namespace {
+// max |G - I| over a k x k matrix: per-block maxima then one block.
+__global__ void __launch_bounds__(256) dev_from_identity_kernel(int k, const double2* G,
+                                                                double* part) {
+  __shared__ double sh[8];
+  double m = 0.0;
+  const size_t total = (size_t)k * k;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % k), j = (int)(t / k);
+    const double2 g = G[t];
+    m = fmax(m, fmax(fabs(g.x - (i == j ? 1.0 : 0.0)), fabs(g.y)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < 8; ++w) r = fmax(r, sh[w]);
+    part[blockIdx.x] = r;
+  }
+}
+__global__ void max_reduce_kernel(int n, const double* part, double* out) {
+  if (threadIdx.x != 0) return;
+  double r = 0.0;
+  for (int i = 0; i < n; ++i) r = fmax(r, part[i]);
+  *out = r;
+}
+// T = (3 I - G) / 2
+__global__ void ns_matrix_kernel(int k, const double2* __restrict__ G, double2* __restrict__ T) {
+  const size_t total = (size_t)k * k;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % k), j = (int)(t / k);
+    const double2 g = G[t];
+    T[t] = make_double2(0.5 * ((i == j ? 3.0 : 0.0) - g.x), -0.5 * g.y);
+  }
+}
+}  // namespace
+
+double deviation_from_identity(chfsi_ctx* ctx, int k, const double2* G) {
+  const unsigned nb = (unsigned)std::min<size_t>(((size_t)k * k + 255) / 256, 512);
+  double* part = (double*)ws_get(ctx, "dfi_part", sizeof(double) * (nb + 2));
+  dev_from_identity_kernel<<<nb, 256, 0, ctx->stream>>>(k, G, part);
+  chfsi_check_launch("dev_from_identity");
+  max_reduce_kernel<<<1, 32, 0, ctx->stream>>>((int)nb, part, part + nb);
+  chfsi_check_launch("max_reduce");
+  double* h = (double*)pinned_get(ctx, 64);
+  CHFSI_CUDA_TRY(cudaMemcpyAsync(h, part + nb, sizeof(double), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+  CHFSI_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return *h;
+}
+
+void ns_matrix(cudaStream_t st, int k, const double2* G, double2* T) {
+  ns_matrix_kernel<<<(unsigned)std::min<size_t>(((size_t)k * k + 255) / 256, 1024), 256, 0, st>>>(
+      k, G, T);
+  chfsi_check_launch("ns_matrix");
 }

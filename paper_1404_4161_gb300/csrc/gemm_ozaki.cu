@@ -5,15 +5,17 @@
 // Rayleigh-Ritz step (Z = H Q, Alg. 1 line 7) to ~2^-43 accuracy with
 // error-free splitting (Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59,
 // 2012): every operand row (A) and column (B) is scaled by a power of two
-// to [-1, 1] and cut into S = 6 slices of 7-bit signed digits
-//     x / scale = sum_{p=1..6} d_p 2^{-7p},  |d_1| <= 128, |d_p| <= 64,
+// to [-1, 1] and cut into S slices of 7-bit signed digits (S = 7 for the
+// n-sized products, 8 for the k x k ones of the reduced eigensolve)
+//     x / scale = sum_{p=1..S} d_p 2^{-7p},  |d_1| <= 128, |d_p| <= 64,
 // which BF16 represents exactly.  Digit products are exact (<= 2^14) and
 // the sum of the pairs with p + q = t over a K chunk of 512 stays within
 // 2^24 (t = 2: 512 * 2^14; t = 7: 512 * 8 * 2^12), so the FP32 tensor-core
 // accumulation of each group t = 2..7 (one TMEM accumulator each) is
-// exact.  Pairs with p + q > 7 are dropped: with the slicing remainder
-// (< 2^-43) they bound the error by ~2^-42 |scale_row| |scale_col| per
-// product.
+// exact; the groups t >= 8 carry weights below 2^-35 of the leading one, so
+// their FP32 rounding stays below 2^-59.  Pairs with p + q > S + 1 are
+// dropped: with the slicing remainder (< 2^-7S) they bound the error by
+// ~2^-(7S-1) |scale_row| |scale_col| per product.
 //
 // The complex product is the real GEMM of the filter kernels:
 // C (M x 2N) = A (M x 2K) * B (2K x 2N), A rows [Re S | Im S] of the left
@@ -38,12 +40,12 @@ using namespace tcx;
 
 namespace {
 
-constexpr int OZ_S = 6;        // slices per operand
+constexpr int OZ_S_MAX = 8;    // slices per operand: 6, 7 or 8
+constexpr int OZ_S_LARGE = 7;  // the n-sized products of QR and Rayleigh-Ritz
 constexpr int OZ_BETA = 7;     // bits per slice
 constexpr int OZ_BK = 32;      // K block (64-byte swizzle rows)
 constexpr int OZ_N = 64;       // tile columns (real)
 constexpr int OZ_KC = 512;     // exact-accumulation K chunk
-constexpr int OZ_GROUPS = 6;   // t = p + q = 2 .. 7
 constexpr int OZ_THREADS = 384;
 
 // Shared-memory descriptor, K-major, 64-byte swizzle: SBO = 8 rows x 64 B.
@@ -81,9 +83,13 @@ struct OzParams {
   int* err;
 };
 
+// OZ_S slices per operand; pairs with p + q <= OZ_S + 1; one TMEM group
+// (64 columns) per t = p + q, so OZ_S <= 8.
+template <int OZ_S>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
 oz_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
                OzParams p) {
+  constexpr int OZ_GROUPS = OZ_S;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t a_slice = BM * OZ_BK * 2;     // 8 KB
@@ -176,7 +182,7 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ C
             for (int qb = 0; qb < OZ_S; ++qb) {
               const int t = pa + qb;  // 0-based: p + q - 2
               if (t > OZ_S - 1) continue;
-              const int g = t < OZ_GROUPS - 1 ? t : OZ_GROUPS - 1;
+              const int g = t;
               const uint32_t acc = (first_k && !(seen & (1u << g))) ? 0u : 1u;
               seen |= 1u << g;
               umma_bf16(tmem + (uint32_t)(g * OZ_N), desc_sw64(sa + pa * a_slice) + adv,
@@ -273,10 +279,11 @@ __device__ __forceinline__ double pow2_scale(double amax) {
   return ldexp(1.0, e);  // > amax
 }
 
+template <int NS>
 __device__ __forceinline__ void slice_value(double v, __nv_bfloat16* out, size_t stride) {
   double r = v;
 #pragma unroll
-  for (int sl = 0; sl < OZ_S; ++sl) {
+  for (int sl = 0; sl < NS; ++sl) {
     const double sc = ldexp(1.0, OZ_BETA * (sl + 1));
     const double d = rint(r * sc);
     r -= d / sc;
@@ -306,6 +313,7 @@ __device__ double block_max(double v, double* sh) {
 // row i = [Re S[:, i] | -Im S[:, i]]  (for Hermitian H this is row i of H;
 // for S = Q it is row i of Q^H).  With mu (device scalar) the diagonal
 // entry S[i, i] is taken as S[i, i] - mu.  Slices: [sl][i][x], pitch P.
+template <int NS>
 __global__ void __launch_bounds__(256)
 oz_slice_a_conjcols_kernel(int rows, int lds, const double2* __restrict__ S, int P,
                            __nv_bfloat16* __restrict__ out, size_t slice_stride,
@@ -325,8 +333,8 @@ oz_slice_a_conjcols_kernel(int rows, int lds, const double2* __restrict__ S, int
   __nv_bfloat16* o = out + (size_t)i * P;
   for (int x = threadIdx.x; x < rows; x += 256) {
     const double re = col[x].x - (x == i ? shift : 0.0);
-    slice_value(re * inv, o + x, slice_stride);
-    slice_value(-col[x].y * inv, o + rows + x, slice_stride);
+    slice_value<NS>(re * inv, o + x, slice_stride);
+    slice_value<NS>(-col[x].y * inv, o + rows + x, slice_stride);
   }
 }
 
@@ -364,6 +372,7 @@ __global__ void oz_add_shift_kernel(int n, int k, const double* mu, const double
 // A rows from rows of S (rows x cols, column-major, lds): row r =
 // [Re S[r, :] | Im S[r, :]].  One block per row (strided reads; S is
 // n x k with small k).
+template <int NS>
 __global__ void __launch_bounds__(256)
 oz_slice_a_rows_kernel(int cols, int lds, const double2* __restrict__ S, int P,
                        __nv_bfloat16* __restrict__ out, size_t slice_stride,
@@ -381,8 +390,8 @@ oz_slice_a_rows_kernel(int cols, int lds, const double2* __restrict__ S, int P,
   __nv_bfloat16* o = out + (size_t)r * P;
   for (int x = threadIdx.x; x < cols; x += 256) {
     const double2 v = S[(size_t)r + (size_t)x * lds];
-    slice_value(v.x * inv, o + x, slice_stride);
-    slice_value(v.y * inv, o + cols + x, slice_stride);
+    slice_value<NS>(v.x * inv, o + x, slice_stride);
+    slice_value<NS>(v.y * inv, o + cols + x, slice_stride);
   }
 }
 
@@ -390,6 +399,7 @@ oz_slice_a_rows_kernel(int cols, int lds, const double2* __restrict__ S, int P,
 // (Re T_j ; -Im T_j), 2j + 1 = (Im T_j ; Re T_j); stored K-major (row 2j of
 // B^T), slices [sl][2j][x], pitch P; scale per real column (same for the
 // pair).
+template <int NS>
 __global__ void __launch_bounds__(256)
 oz_slice_b_kernel(int rows, int ldt, const double2* __restrict__ T, int P,
                   __nv_bfloat16* __restrict__ out, size_t slice_stride,
@@ -409,10 +419,10 @@ oz_slice_b_kernel(int rows, int ldt, const double2* __restrict__ T, int P,
   __nv_bfloat16* o1 = o0 + P;
   for (int x = threadIdx.x; x < rows; x += 256) {
     const double re = col[x].x * inv, im = col[x].y * inv;
-    slice_value(re, o0 + x, slice_stride);
-    slice_value(-im, o0 + rows + x, slice_stride);
-    slice_value(im, o1 + x, slice_stride);
-    slice_value(re, o1 + rows + x, slice_stride);
+    slice_value<NS>(re, o0 + x, slice_stride);
+    slice_value<NS>(-im, o0 + rows + x, slice_stride);
+    slice_value<NS>(im, o1 + x, slice_stride);
+    slice_value<NS>(re, o1 + rows + x, slice_stride);
   }
 }
 
@@ -459,7 +469,8 @@ CUtensorMap make_map3(const void* base, int inner, int rows, int P, int slices, 
 
 // Sliced operand storage and the launch.
 struct OzOperand {
-  __nv_bfloat16* data = nullptr;  // OZ_S slices
+  __nv_bfloat16* data = nullptr;  // ns slices
+  int ns = 6;
   double* scale = nullptr;
   int rows = 0;      // M (A) or 2N (B)
   int K2 = 0;        // real K
@@ -467,20 +478,23 @@ struct OzOperand {
   size_t stride = 0; // elements per slice
 };
 
-static void oz_alloc(chfsi_ctx* ctx, const std::string& name, OzOperand& o, int rows, int K2) {
+static void oz_alloc(chfsi_ctx* ctx, const std::string& name, OzOperand& o, int rows, int K2,
+                     int ns) {
+  o.ns = ns;
   o.rows = rows;
   o.K2 = K2;
   o.P = (K2 + 7) / 8 * 8;
   o.stride = (size_t)rows * o.P;
   o.data = (__nv_bfloat16*)ws_get(ctx, (name + ".sl").c_str(),
-                                  sizeof(__nv_bfloat16) * OZ_S * o.stride + 256);
+                                  sizeof(__nv_bfloat16) * ns * o.stride + 256);
   o.scale = (double*)ws_get(ctx, (name + ".sc").c_str(), sizeof(double) * (rows + 8));
 }
 
 // C (M x Nc complex) = alpha * left * right + beta * C, where the left factor
 // is given as A rows (already sliced) and the right factor as B (sliced).
-static void oz_run(chfsi_ctx* ctx, const OzOperand& A, const OzOperand& B, double2* C, int ldc,
-                   double alpha, double beta) {
+template <int OZ_S>
+static void oz_run_t(chfsi_ctx* ctx, const OzOperand& A, const OzOperand& B, double2* C,
+                     int ldc, double alpha, double beta) {
   cudaStream_t st = ctx->stream;
   const int M = A.rows, N2 = B.rows, K2 = A.K2;
   const int kblocks = (K2 + OZ_BK - 1) / OZ_BK;
@@ -499,7 +513,7 @@ static void oz_run(chfsi_ctx* ctx, const OzOperand& A, const OzOperand& B, doubl
   const size_t smem = 1024 + (size_t)stages * stage_bytes + 8 * (2 * stages + 2) + 32;
   static bool attr = false;
   if (!attr) {
-    CHFSI_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel,
+    CHFSI_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel<OZ_S>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     attr = true;
   }
@@ -532,7 +546,7 @@ static void oz_run(chfsi_ctx* ctx, const OzOperand& A, const OzOperand& B, doubl
   }
   dim3 grid(nt, mt, splits);
   const int slot = kt_begin(st);
-  oz_gemm_kernel<<<grid, OZ_THREADS, smem, st>>>(mA, mB, p);
+  oz_gemm_kernel<OZ_S><<<grid, OZ_THREADS, smem, st>>>(mA, mB, p);
   chfsi_check_launch("oz_gemm");
   kt_end(st, slot, KT_F64, 8.0 * (double)M * Nc * (K2 / 2));
   if (!direct) {
@@ -543,6 +557,16 @@ static void oz_run(chfsi_ctx* ctx, const OzOperand& A, const OzOperand& B, doubl
   }
 }
 
+static void oz_run(chfsi_ctx* ctx, const OzOperand& A, const OzOperand& B, double2* C, int ldc,
+                   double alpha, double beta) {
+  if (A.ns == 8)
+    oz_run_t<8>(ctx, A, B, C, ldc, alpha, beta);
+  else if (A.ns == 7)
+    oz_run_t<7>(ctx, A, B, C, ldc, alpha, beta);
+  else
+    oz_run_t<6>(ctx, A, B, C, ldc, alpha, beta);
+}
+
 int oz_check_error(chfsi_ctx* ctx) {
   int* h = (int*)pinned_get(ctx, 64);
   CHFSI_CUDA_TRY(cudaMemcpyAsync(h, ws_get(ctx, "oz_err", sizeof(int)), sizeof(int),
@@ -550,6 +574,32 @@ int oz_check_error(chfsi_ctx* ctx) {
   CHFSI_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   return *h;
 }
+
+template <int NS>
+static void oz_slice_a_conj(cudaStream_t st, int nrows_S, int lds, const double2* S, int count,
+                            const OzOperand& A, const double* mu) {
+  oz_slice_a_conjcols_kernel<NS><<<count, 256, 0, st>>>(nrows_S, lds, S, A.P, A.data, A.stride,
+                                                        A.scale, mu);
+  chfsi_check_launch("oz_slice_a_conj");
+}
+template <int NS>
+static void oz_slice_a_row(cudaStream_t st, int cols, int lds, const double2* S, int count,
+                           const OzOperand& A) {
+  oz_slice_a_rows_kernel<NS><<<count, 256, 0, st>>>(cols, lds, S, A.P, A.data, A.stride, A.scale);
+  chfsi_check_launch("oz_slice_a_rows");
+}
+template <int NS>
+static void oz_slice_bb(cudaStream_t st, int rows, int ldt, const double2* T, int count,
+                        const OzOperand& B) {
+  oz_slice_b_kernel<NS><<<count, 256, 0, st>>>(rows, ldt, T, B.P, B.data, B.stride, B.scale);
+  chfsi_check_launch("oz_slice_b");
+}
+#define OZ_DISPATCH(ns, fn, ...)          \
+  do {                                    \
+    if ((ns) == 8) fn<8>(__VA_ARGS__);    \
+    else if ((ns) == 7) fn<7>(__VA_ARGS__); \
+    else fn<6>(__VA_ARGS__);              \
+  } while (0)
 
 // Z (n x k) = H Q with H Hermitian n x n, both complex column-major,
 // computed as (H - mu I) Q + mu Q with mu = mean(Re diag H): the diagonal of
@@ -559,18 +609,15 @@ int oz_check_error(chfsi_ctx* ctx) {
 void oz_hemm(chfsi_ctx* ctx, const std::string& prefix, const double2* H, int n,
              const double2* Q, int k, double2* Z, bool reslice_h) {
   OzOperand A, B;
-  oz_alloc(ctx, prefix + "ozH", A, n, 2 * n);
+  oz_alloc(ctx, prefix + "ozH", A, n, 2 * n, OZ_S_LARGE);
   double* mu = (double*)ws_get(ctx, (prefix + "ozH.mu").c_str(), sizeof(double));
   if (reslice_h) {
     oz_diag_mean_kernel<<<1, 256, 0, ctx->stream>>>(n, H, mu);
     chfsi_check_launch("oz_diag_mean");
-    oz_slice_a_conjcols_kernel<<<n, 256, 0, ctx->stream>>>(n, n, H, A.P, A.data, A.stride,
-                                                           A.scale, mu);
-    chfsi_check_launch("oz_slice_h");
+    oz_slice_a_conj<OZ_S_LARGE>(ctx->stream, n, n, H, n, A, mu);
   }
-  oz_alloc(ctx, "ozQ", B, 2 * k, 2 * n);
-  oz_slice_b_kernel<<<k, 256, 0, ctx->stream>>>(n, n, Q, B.P, B.data, B.stride, B.scale);
-  chfsi_check_launch("oz_slice_b");
+  oz_alloc(ctx, "ozQ", B, 2 * k, 2 * n, OZ_S_LARGE);
+  oz_slice_bb<OZ_S_LARGE>(ctx->stream, n, n, Q, k, B);
   oz_run(ctx, A, B, Z, n, 1.0, 0.0);
   const size_t total = (size_t)n * k;
   oz_add_shift_kernel<<<(unsigned)std::min<size_t>((total + 255) / 256, 4096), 256, 0,
@@ -580,28 +627,24 @@ void oz_hemm(chfsi_ctx* ctx, const std::string& prefix, const double2* H, int n,
 
 // C (k1 x k2) = alpha * L^H R + beta * C with L n x k1, R n x k2.
 void oz_gemm_cn(chfsi_ctx* ctx, int k1, int k2, int n, const double2* L, int ldl,
-                const double2* R, int ldr, double2* C, int ldc, double alpha, double beta) {
+                const double2* R, int ldr, double2* C, int ldc, double alpha, double beta,
+                int ns) {
   OzOperand A, B;
-  oz_alloc(ctx, "ozL", A, k1, 2 * n);
-  oz_slice_a_conjcols_kernel<<<k1, 256, 0, ctx->stream>>>(n, ldl, L, A.P, A.data, A.stride,
-                                                          A.scale, nullptr);
-  chfsi_check_launch("oz_slice_l");
-  oz_alloc(ctx, "ozR", B, 2 * k2, 2 * n);
-  oz_slice_b_kernel<<<k2, 256, 0, ctx->stream>>>(n, ldr, R, B.P, B.data, B.stride, B.scale);
-  chfsi_check_launch("oz_slice_r");
+  oz_alloc(ctx, "ozL", A, k1, 2 * n, ns);
+  OZ_DISPATCH(ns, oz_slice_a_conj, ctx->stream, n, ldl, L, k1, A, nullptr);
+  oz_alloc(ctx, "ozR", B, 2 * k2, 2 * n, ns);
+  OZ_DISPATCH(ns, oz_slice_bb, ctx->stream, n, ldr, R, k2, B);
   oz_run(ctx, A, B, C, ldc, alpha, beta);
 }
 
 // C (m x k2) = alpha * S W + beta * C with S m x k1 (lds), W k1 x k2 (ldw).
 void oz_gemm_nn(chfsi_ctx* ctx, int m, int k2, int k1, const double2* S, int lds,
-                const double2* W, int ldw, double2* C, int ldc, double alpha, double beta) {
+                const double2* W, int ldw, double2* C, int ldc, double alpha, double beta,
+                int ns) {
   OzOperand A, B;
-  oz_alloc(ctx, "ozS", A, m, 2 * k1);
-  oz_slice_a_rows_kernel<<<m, 256, 0, ctx->stream>>>(k1, lds, S, A.P, A.data, A.stride,
-                                                     A.scale);
-  chfsi_check_launch("oz_slice_s");
-  oz_alloc(ctx, "ozW", B, 2 * k2, 2 * k1);
-  oz_slice_b_kernel<<<k2, 256, 0, ctx->stream>>>(k1, ldw, W, B.P, B.data, B.stride, B.scale);
-  chfsi_check_launch("oz_slice_w");
+  oz_alloc(ctx, "ozS", A, m, 2 * k1, ns);
+  OZ_DISPATCH(ns, oz_slice_a_row, ctx->stream, k1, lds, S, m, A);
+  oz_alloc(ctx, "ozW", B, 2 * k2, 2 * k1, ns);
+  OZ_DISPATCH(ns, oz_slice_bb, ctx->stream, k1, ldw, W, k2, B);
   oz_run(ctx, A, B, C, ldc, alpha, beta);
 }
