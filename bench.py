@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--degrees", choices=["learned", "analytic"], default="learned")
+    ap.add_argument("--warm-rr", action="store_true",
+                    help="Rayleigh-Ritz on each warm start before the first filter")
     ap.add_argument("--f64-gemm", choices=["ozaki", "fp64"], default="ozaki",
                     help="engine of the FP64 products in the tc/mixed modes")
     ap.add_argument("--batched-scale", type=float, default=0.25,
@@ -273,7 +275,8 @@ def main():
 
     prec = {"tc": L.PREC_TC, "mixed": L.PREC_MIXED, "fp64": L.PREC_FP64}[args.precision]
     f64g = L.GEMM_OZAKI if (args.f64_gemm == "ozaki" and prec != L.PREC_FP64) else L.GEMM_FP64
-    s = Chfsi(precision=prec, profile=1, f64_gemm=f64g)
+    warm_rr = 1 if (prec == L.PREC_TC and args.warm_rr) else 0
+    s = Chfsi(precision=prec, profile=1, f64_gemm=f64g, warm_rr=warm_rr)
     stream = torch.cuda.current_stream()
     train_info = None
     if args.degrees == "learned":
@@ -450,6 +453,7 @@ def main():
                                    f"delta=1e-4, tol 1e-10",
                        "precision": args.precision, "degree_model": args.degrees,
                        "f64_products": "ozaki (tensor cores)" if f64g == L.GEMM_OZAKI else "fp64 pipe",
+                       "warm_rayleigh_ritz": bool(warm_rr),
                        "l2": "inputs larger than L2 (each H is 16 n^2 bytes)",
                        "parallelism": f"replicas x{ws}"},
             "filter_tflops": filter_tflops,

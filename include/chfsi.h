@@ -88,6 +88,10 @@ typedef struct chfsi_opts {
   int step0;           /* sequence index of the next problem solved (0):  */
                        /* the step feature of the degree MLP and traces   */
   int f64_gemm;        /* CHFSI_GEMM_FP64 / CHFSI_GEMM_OZAKI        (FP64) */
+  int warm_rr;         /* 1: on a warm start, Rayleigh-Ritz the starting  */
+                       /* block before the first filter, so the first loop */
+                       /* gets per-vector degrees and (CHFSI_PREC_TC) the  */
+                       /* refinement form (0: the paper's uniform deg)     */
 } chfsi_opts;
 
 /* Per-problem statistics (host struct, filled when non-NULL). */

@@ -26,7 +26,7 @@ class Opts(C.Structure):
                 ("deg_max", C.c_int), ("deg_extra", C.c_int), ("lanczos_steps", C.c_int),
                 ("max_loops", C.c_int), ("switch_tol", C.c_double), ("seed", C.c_ulonglong),
                 ("profile", C.c_int), ("mlp_extra", C.c_int), ("step0", C.c_int),
-                ("f64_gemm", C.c_int)]
+                ("f64_gemm", C.c_int), ("warm_rr", C.c_int)]
 
 
 class Stats(C.Structure):

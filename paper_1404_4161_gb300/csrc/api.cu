@@ -437,6 +437,7 @@ struct Problem {
   double* psi = nullptr;  // refinement tables of the current loop
   double* fR = nullptr;
   bool h_sliced = false;  // tensor-core slices of H built for this problem
+  bool have_R = false;    // residual block of the current Ritz pairs built
 
   void* ws(const char* name, size_t bytes) { return ws_get(ctx, (pre + name).c_str(), bytes); }
   void mark(int i) { CHFSI_CUDA_TRY(cudaEventRecord(ev[i], st)); }
@@ -535,6 +536,18 @@ struct Problem {
     use_mlp = o->degree_model == CHFSI_DEG_MLP;
     trace_abandon(ctx);
     lowp_on = mixed;
+    if (warm && o->warm_rr) {
+      // Rayleigh-Ritz on the (orthonormal) warm block: residuals, locking
+      // and degrees are known before the first filter.
+      mark(3);
+      mark(4);
+      rayleigh_ritz_dev(ctx, H, n, ka, Xact, Yrr, HY, lam, pre, &h_sliced);
+      mark(5);
+      residual_norms(st, n, ka, HY, Yrr, lam, norm_h, res);
+      mark(6);
+      after_rr();
+      S.ms_rr += ms(4, 5);
+    }
   }
 
   double c_() const { return 0.5 * (alpha + beta); }
@@ -549,7 +562,7 @@ struct Problem {
     for (int j = 0; j < ka; ++j) sdeg += degs[j];
     mark(2);
     fl0 = chfsi_launch_counter();
-    if (tc_all) return loops == 1 ? TC_PLAIN : TC_DEFECT;
+    if (tc_all) return have_R ? TC_DEFECT : TC_PLAIN;
     if (lowp_on) return TC_PLAIN;
     return F64;
   }
@@ -606,6 +619,16 @@ struct Problem {
     residual_norms(st, n, ka, HY, Yrr, lam, norm_h, res);
     trace_finish(ctx, ka, res);
     mark(6);
+    after_rr();
+    S.ms_filter += ms(2, 3);
+    S.ms_qr += ms(3, 4);
+    S.ms_rr += ms(4, 5);
+    S.ms_resid += ms(5, 6);
+    S.ms_lock += ms(6, 7);
+  }
+
+  // Locking, interval update, degrees and sort after a Rayleigh-Ritz step.
+  void after_rr() {
     lock_select(st, ka, lam, res, nev - nl, tol, gamma, ctl, lock_idx, act_idx);
     char* hp = (char*)pinned_get(ctx, 1024 + sizeof(int) * (size_t)k + sizeof(double) * k);
     LoopCtl* ctl_h = (LoopCtl*)(hp + 256);
@@ -653,7 +676,10 @@ struct Problem {
       trace_record(ctx, ka, lam, res, act_idx, deg, c2, e2, gamma, step, nev - nl);
       sort_by_degree(st, ka, deg, act_idx, perm, deg_sorted);
       gather_columns(st, n, ka, Yrr, n, perm, Xact, n);
-      if (tc_all) residual_block(st, n, ka, HY, Yrr, lam, perm, Rblk, lam_act);
+      if (tc_all) {
+        residual_block(st, n, ka, HY, Yrr, lam, perm, Rblk, lam_act);
+        have_R = true;
+      }
       CHFSI_CUDA_TRY(cudaMemcpyAsync(deg_h, deg_sorted, sizeof(int) * ka,
                                      cudaMemcpyDeviceToHost, st));
       mark(7);
@@ -661,11 +687,6 @@ struct Problem {
       degs.assign(deg_h, deg_h + ka);
       if (loops >= o->max_loops) done = true;
     }
-    S.ms_filter += ms(2, 3);
-    S.ms_qr += ms(3, 4);
-    S.ms_rr += ms(4, 5);
-    S.ms_resid += ms(5, 6);
-    S.ms_lock += ms(6, 7);
   }
 
   // Output: locked pairs ascending, then the remaining active block.
@@ -836,6 +857,7 @@ void chfsi_default_opts(chfsi_opts* o) {
   o->mlp_extra = 2;
   o->step0 = 0;
   o->f64_gemm = CHFSI_GEMM_FP64;
+  o->warm_rr = 0;
 }
 
 const char* chfsi_strerror(int code) {

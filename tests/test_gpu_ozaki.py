@@ -167,3 +167,30 @@ def test_rayleigh_ritz_mixed_eigensolver(ctx, n, k):
     r_gpu = np.linalg.norm(H @ Y - Y * ev[None, :], axis=0) / normH
     r_ref = np.linalg.norm(H @ Yr - Yr * lr[None, :], axis=0) / normH
     assert np.all(r_gpu <= r_ref * (1 + 1e-9) + 1e-13)
+
+
+def test_sequence_warm_rayleigh_ritz():
+    """opts.warm_rr: a Rayleigh-Ritz step on each warm start before the
+    first filter (degrees and the refinement form from the first loop):
+    same eigenpairs, fewer loops than without it."""
+    from paper_1404_4161_gb300.build import build
+    build()
+    cfg2 = CONFIGS[2]
+    n, nev, nex = 1024, 64, 16
+    Hs, lam2 = config_sequence(cfg2, BASE_SEED + 2200, length=4, n=n, delta=0.0)
+    loops = {}
+    for wr in (0, 1):
+        s = Chfsi(precision=L.PREC_TC, f64_gemm=L.GEMM_OZAKI, warm_rr=wr)
+        Xc = to_dev_cm(random_block(n, nev + nex, BASE_SEED + 2600))
+        ev, sts, rc = s.solve_sequence([to_dev_cm(h) for h in Hs], nev, nex, Xc, 1e-10)
+        s.close()
+        assert rc == L.OK
+        ev = ev.cpu().numpy()
+        for l in range(4):
+            assert np.abs(ev[l, :nev] - lam2[:nev]).max() <= 1e-12 * np.abs(lam2).max()
+        X = from_dev_cm(Xc)
+        R = np.linalg.norm(Hs[-1] @ X[:, :nev] - X[:, :nev] * ev[-1, :nev], axis=0)
+        assert R.max() / np.abs(lam2).max() <= 1e-10
+        loops[wr] = [t["loops"] for t in sts]
+    print("loops without / with warm RR", loops)
+    assert sum(loops[1][1:]) < sum(loops[0][1:])
