@@ -272,39 +272,74 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ C
 }
 
 // ---- operand slicing ------------------------------------------------------
-__device__ __forceinline__ double pow2_scale(double amax) {
-  if (!(amax > 0.0)) return 1.0;
-  int e;
-  frexp(amax, &e);  // amax = f 2^e, f in [0.5, 1)
-  return ldexp(1.0, e);  // > amax
+// Integer-only slicing (the FP64 pipe is too narrow for per-digit FP64 math):
+// |x| and the row/column maximum come from the IEEE bit patterns, the scaled
+// value N = round(x 2^(7 NS) / 2^s) is formed by shifting the 53-bit
+// significand, and the digits are balanced base-128 digits of N (least
+// significant first, d in [-64, 63], the leading digit takes the rest and
+// stays within +-128).  sum_p d_p 2^{-7p} = N 2^{-7 NS} exactly, and
+// |x / 2^s - N 2^{-7 NS}| <= 2^{-7 NS - 1}.
+
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// s with 2^s > |x| for the largest |x| whose bit pattern is `mb` (0 -> 0).
+__device__ __forceinline__ int pow2_exponent(unsigned long long mb) {
+  if (mb == 0) return 0;
+  const int e = (int)(mb >> 52);                // biased exponent
+  if (e == 0) return -1022;                     // subnormal: 2^-1022 > |x|
+  return e - 1023 + 1;                          // |x| < 2^(e - 1022)
 }
 
 template <int NS>
-__device__ __forceinline__ void slice_value(double v, __nv_bfloat16* out, size_t stride) {
-  double r = v;
-#pragma unroll
-  for (int sl = 0; sl < NS; ++sl) {
-    const double sc = ldexp(1.0, OZ_BETA * (sl + 1));
-    const double d = rint(r * sc);
-    r -= d / sc;
-    out[(size_t)sl * stride] = __double2bfloat16(d);
+__device__ __forceinline__ void slice_value(double x, int s, __nv_bfloat16* out, size_t stride) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  const bool neg = (bits >> 63) != 0;
+  const int e = (int)((bits >> 52) & 0x7FF);
+  unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
+  if (e != 0) m |= 1ull << 52;
+  // x = m 2^(max(e,1) - 1075); N = round(m 2^sh), sh = max(e,1) - 1075 + 7 NS - s
+  const int sh = (e ? e : 1) - 1075 + 7 * NS - s;
+  long long N = 0;
+  if (m != 0) {
+    if (sh >= 0) {
+      N = (long long)(m << sh);  // |x| < 2^s keeps N below 2^(7 NS) <= 2^56
+    } else if (sh > -64) {
+      const int r = -sh;
+      N = (long long)((m + (1ull << (r - 1))) >> r);
+    }
   }
+  if (neg) N = -N;
+#pragma unroll
+  for (int p = NS - 1; p > 0; --p) {
+    int d = (int)(N & 127);
+    if (d >= 64) d -= 128;
+    N = (N - d) >> 7;
+    out[(size_t)p * stride] = __int2bfloat16_rn(d);
+  }
+  out[0] = __int2bfloat16_rn((int)N);
 }
 
-template <int NT>
-__device__ double block_max(double v, double* sh) {
+__device__ unsigned long long block_max_bits(unsigned long long v, unsigned long long* sh) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = u > v ? u : v;
+  }
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x < 32) {
-    v = threadIdx.x < NT / 32 ? sh[threadIdx.x] : 0.0;
+    v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0ull;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+      v = u > v ? u : v;
+    }
     if (threadIdx.x == 0) sh[0] = v;
   }
   __syncthreads();
-  const double r = sh[0];
+  const unsigned long long r = sh[0];
   __syncthreads();
   return r;
 }
@@ -318,23 +353,24 @@ __global__ void __launch_bounds__(256)
 oz_slice_a_conjcols_kernel(int rows, int lds, const double2* __restrict__ S, int P,
                            __nv_bfloat16* __restrict__ out, size_t slice_stride,
                            double* __restrict__ scale, const double* __restrict__ mu) {
-  __shared__ double sh[8];
+  __shared__ unsigned long long sh[8];
   const int i = blockIdx.x;
   const double2* col = S + (size_t)i * lds;
   const double shift = mu ? *mu : 0.0;
-  double m = 0.0;
+  unsigned long long m = 0;
   for (int x = threadIdx.x; x < rows; x += 256) {
-    const double re = col[x].x - (x == i ? shift : 0.0);
-    m = fmax(m, fmax(fabs(re), fabs(col[x].y)));
+    const double re = (x == i) ? col[x].x - shift : col[x].x;
+    const unsigned long long a = abs_bits(re), b = abs_bits(col[x].y);
+    m = a > m ? a : m;
+    m = b > m ? b : m;
   }
-  const double sc = pow2_scale(block_max<256>(m, sh));
-  if (threadIdx.x == 0) scale[i] = sc;
-  const double inv = 1.0 / sc;
+  const int se = pow2_exponent(block_max_bits(m, sh));
+  if (threadIdx.x == 0) scale[i] = ldexp(1.0, se);
   __nv_bfloat16* o = out + (size_t)i * P;
   for (int x = threadIdx.x; x < rows; x += 256) {
-    const double re = col[x].x - (x == i ? shift : 0.0);
-    slice_value<NS>(re * inv, o + x, slice_stride);
-    slice_value<NS>(-col[x].y * inv, o + rows + x, slice_stride);
+    const double re = (x == i) ? col[x].x - shift : col[x].x;
+    slice_value<NS>(re, se, o + x, slice_stride);
+    slice_value<NS>(-col[x].y, se, o + rows + x, slice_stride);
   }
 }
 
@@ -370,28 +406,58 @@ __global__ void oz_add_shift_kernel(int n, int k, const double* mu, const double
 }
 
 // A rows from rows of S (rows x cols, column-major, lds): row r =
-// [Re S[r, :] | Im S[r, :]].  One block per row (strided reads; S is
-// n x k with small k).
+// [Re S[r, :] | Im S[r, :]].  A block takes 32 rows; the maximum pass reads
+// 32 consecutive rows per column (coalesced) and combines the row maxima in
+// shared memory.
 template <int NS>
 __global__ void __launch_bounds__(256)
-oz_slice_a_rows_kernel(int cols, int lds, const double2* __restrict__ S, int P,
+oz_slice_a_rows_kernel(int nrows, int cols, int lds, const double2* __restrict__ S, int P,
                        __nv_bfloat16* __restrict__ out, size_t slice_stride,
                        double* __restrict__ scale) {
-  __shared__ double sh[8];
-  const int r = blockIdx.x;
-  double m = 0.0;
-  for (int x = threadIdx.x; x < cols; x += 256) {
-    const double2 v = S[(size_t)r + (size_t)x * lds];
-    m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+  __shared__ unsigned long long shm[8][32];
+  __shared__ int sexp[32];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int r = blockIdx.x * 32 + tx;
+  unsigned long long m = 0;
+  if (r < nrows)
+    for (int x = ty; x < cols; x += 8) {
+      const double2 v = S[(size_t)r + (size_t)x * lds];
+      const unsigned long long a = abs_bits(v.x), b = abs_bits(v.y);
+      m = a > m ? a : m;
+      m = b > m ? b : m;
+    }
+  shm[ty][tx] = m;
+  __syncthreads();
+  if (ty == 0) {
+    unsigned long long mm = 0;
+    for (int t = 0; t < 8; ++t) mm = shm[t][tx] > mm ? shm[t][tx] : mm;
+    const int se = pow2_exponent(mm);
+    sexp[tx] = se;
+    if (r < nrows) scale[r] = ldexp(1.0, se);
   }
-  const double sc = pow2_scale(block_max<256>(m, sh));
-  if (threadIdx.x == 0) scale[r] = sc;
-  const double inv = 1.0 / sc;
-  __nv_bfloat16* o = out + (size_t)r * P;
-  for (int x = threadIdx.x; x < cols; x += 256) {
-    const double2 v = S[(size_t)r + (size_t)x * lds];
-    slice_value<NS>(v.x * inv, o + x, slice_stride);
-    slice_value<NS>(v.y * inv, o + cols + x, slice_stride);
+  __syncthreads();
+  // 32 x 32 tiles through shared memory so that the slice stores run along
+  // the row (coalesced) while the loads run down the column.
+  __shared__ double2 tile[32][33];
+  const int r0 = blockIdx.x * 32;
+  for (int x0 = 0; x0 < cols; x0 += 32) {
+#pragma unroll
+    for (int c = ty; c < 32; c += 8) {
+      const int x = x0 + c;
+      tile[c][tx] = (r < nrows && x < cols) ? S[(size_t)r + (size_t)x * lds] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    const int x = x0 + tx;
+#pragma unroll
+    for (int rr = ty; rr < 32; rr += 8) {
+      if (r0 + rr < nrows && x < cols) {
+        const double2 v = tile[tx][rr];
+        __nv_bfloat16* o = out + (size_t)(r0 + rr) * P;
+        slice_value<NS>(v.x, sexp[rr], o + x, slice_stride);
+        slice_value<NS>(v.y, sexp[rr], o + cols + x, slice_stride);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -404,25 +470,28 @@ __global__ void __launch_bounds__(256)
 oz_slice_b_kernel(int rows, int ldt, const double2* __restrict__ T, int P,
                   __nv_bfloat16* __restrict__ out, size_t slice_stride,
                   double* __restrict__ scale) {
-  __shared__ double sh[8];
+  __shared__ unsigned long long sh[8];
   const int j = blockIdx.x;
   const double2* col = T + (size_t)j * ldt;
-  double m = 0.0;
-  for (int x = threadIdx.x; x < rows; x += 256) m = fmax(m, fmax(fabs(col[x].x), fabs(col[x].y)));
-  const double sc = pow2_scale(block_max<256>(m, sh));
-  if (threadIdx.x == 0) {
-    scale[2 * j] = sc;
-    scale[2 * j + 1] = sc;
+  unsigned long long m = 0;
+  for (int x = threadIdx.x; x < rows; x += 256) {
+    const unsigned long long a = abs_bits(col[x].x), b = abs_bits(col[x].y);
+    m = a > m ? a : m;
+    m = b > m ? b : m;
   }
-  const double inv = 1.0 / sc;
+  const int se = pow2_exponent(block_max_bits(m, sh));
+  if (threadIdx.x == 0) {
+    scale[2 * j] = ldexp(1.0, se);
+    scale[2 * j + 1] = ldexp(1.0, se);
+  }
   __nv_bfloat16* o0 = out + (size_t)(2 * j) * P;
   __nv_bfloat16* o1 = o0 + P;
   for (int x = threadIdx.x; x < rows; x += 256) {
-    const double re = col[x].x * inv, im = col[x].y * inv;
-    slice_value<NS>(re, o0 + x, slice_stride);
-    slice_value<NS>(-im, o0 + rows + x, slice_stride);
-    slice_value<NS>(im, o1 + x, slice_stride);
-    slice_value<NS>(re, o1 + rows + x, slice_stride);
+    const double re = col[x].x, im = col[x].y;
+    slice_value<NS>(re, se, o0 + x, slice_stride);
+    slice_value<NS>(-im, se, o0 + rows + x, slice_stride);
+    slice_value<NS>(im, se, o1 + x, slice_stride);
+    slice_value<NS>(re, se, o1 + rows + x, slice_stride);
   }
 }
 
@@ -585,7 +654,8 @@ static void oz_slice_a_conj(cudaStream_t st, int nrows_S, int lds, const double2
 template <int NS>
 static void oz_slice_a_row(cudaStream_t st, int cols, int lds, const double2* S, int count,
                            const OzOperand& A) {
-  oz_slice_a_rows_kernel<NS><<<count, 256, 0, st>>>(cols, lds, S, A.P, A.data, A.stride, A.scale);
+  oz_slice_a_rows_kernel<NS><<<(count + 31) / 32, 256, 0, st>>>(count, cols, lds, S, A.P, A.data,
+                                                                A.stride, A.scale);
   chfsi_check_launch("oz_slice_a_rows");
 }
 template <int NS>
