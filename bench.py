@@ -134,8 +134,8 @@ def run_reference(args):
         return
     import torch
     import oracle
-    from workloads.synthetic import CONFIGS, random_block
-    cfg = CONFIGS[2]
+    from workloads.synthetic import WORKLOADS, random_block
+    cfg = WORKLOADS["seq10_n4096"]
     n = args.n or cfg.n
     nev, nex = sizes(cfg, n)
     length = args.length or cfg.length
@@ -199,8 +199,8 @@ def measure_batched(scale, dev, stream, prec):
     import torch
     from paper_1404_4161_gb300 import _lib as L
     from paper_1404_4161_gb300.solver import Chfsi, colmajor
-    from workloads.synthetic import CONFIGS, config_sequence, random_block
-    cfg = CONFIGS[4]
+    from workloads.synthetic import WORKLOADS, config_sequence, random_block
+    cfg = WORKLOADS["batched64"]
     rng = np.random.Generator(np.random.PCG64(14044161 + 4000))
     lo, hi = int(1500 * scale), int(6000 * scale)
     seqs, steps = [], 2
@@ -258,9 +258,9 @@ def main():
         dist.barrier()
     from paper_1404_4161_gb300 import _lib as L
     from paper_1404_4161_gb300.solver import Chfsi, colmajor
-    from workloads.synthetic import CONFIGS, random_block
+    from workloads.synthetic import WORKLOADS, random_block
 
-    cfg = CONFIGS[2]
+    cfg = WORKLOADS["seq10_n4096"]
     n = args.n or cfg.n
     nev, nex = sizes(cfg, n)
     k = nev + nex

@@ -63,7 +63,7 @@ extern "C" {
                             /* products, exact FP32 chunk sums (~2^-48 of    */
                             /* row scale x column scale per product)         */
 
-/* Degree model (Alg. 1 line 11). */
+/* Degree model (degree optimisation of Alg. 1). */
 #define CHFSI_DEG_ANALYTIC 0 /* Single Optimization rule of Sec. 3.2         */
 #define CHFSI_DEG_MLP 1      /* learned predictor; analytic rule as fallback */
 
@@ -149,7 +149,7 @@ const char* chfsi_last_error(const chfsi_ctx* ctx);
 /* Solve one problem: the nev lowest eigenpairs of the Hermitian H
  * (Alg. 1; Alg. 2 for the filter).
  *  H      complex n x n, Hermitian, read only (shift and scale of Alg. 2
- *         line 1 are folded into the filter; H is never written).
+ *         are folded into the filter; H is never written).
  *  X      complex n x (nev+nex); in: starting block X0, out: the block of
  *         Ritz vectors, the locked (converged) pairs first, ascending.
  *  evals  n_ev = nev+nex doubles (device), ascending within the locked part
@@ -203,7 +203,7 @@ int chfsi_solve_batched(chfsi_ctx* ctx, int P, const chfsi_problem* probs, int s
 
 /* ---- the steps of the hot path, one entry point each ------------------ */
 
-/* Alg. 1 line 3: s-step Lanczos with full reorthogonalisation from the
+/* Alg. 1 (spectral bounds): s-step Lanczos with full reorthogonalisation from the
  * SplitMix64 start vector of `seed` (entry j = u(2j) + i u(2j+1), u(t) =
  * 2 (splitmix64_t >> 11) 2^-53 - 1).  out_host[0..3] = {beta = theta_max +
  * ||f||, theta_min, theta_max, ||H||_est = max(|theta_min|, |theta_max|)}. */
@@ -262,7 +262,7 @@ int chfsi_filter_refine(chfsi_ctx* ctx, const double* H, int n, int k, const dou
 int chfsi_zgemm(chfsi_ctx* ctx, int op_a, int m, int n, int k, double alpha, const double* A,
                 int lda, const double* B, int ldb, double beta, double* C, int ldc, int engine);
 
-/* Alg. 1 line 6: orthonormalise the k columns of Y (complex n x k, in
+/* Alg. 1 (QR step): orthonormalise the k columns of Y (complex n x k, in
  * place) against the nl orthonormal columns of L (complex n x nl; may be
  * NULL when nl = 0) by two block Gram-Schmidt passes and CholQR2 (shifted
  * CholQR3 when the Gram matrix is not numerically positive definite).
@@ -271,7 +271,7 @@ int chfsi_zgemm(chfsi_ctx* ctx, int op_a, int m, int n, int k, double alpha, con
 int chfsi_orthonormalize(chfsi_ctx* ctx, int n, int nl, const double* L, int k,
                          double* Y);
 
-/* Alg. 1 lines 7-9: Rayleigh-Ritz on orthonormal Q (complex n x k):
+/* Alg. 1: Rayleigh-Ritz on orthonormal Q (complex n x k):
  * Z = HQ, G = Q^H Z (Hermitianised), G W = W Lambda, Y = QW, HY = ZW.
  * Y and HY: complex n x k outputs; evals: k doubles, ascending. */
 int chfsi_rayleigh_ritz(chfsi_ctx* ctx, const double* H, int n, int k,
@@ -325,7 +325,7 @@ int chfsi_filter_static(const double* H, int n, int k, const double* Y0,
 
 /* ---- learned degree predictor (not in the paper) ---------------------- */
 
-/* Traces for training (Alg. 1 line 11 decisions and their outcome).
+/* Traces for training (Alg. 1 degree decisions and their outcome).
  * chfsi_trace_enable(ctx, cap) starts recording, into a device buffer of
  * cap rows owned by the context (cap = 0 stops and frees it): for every
  * active column of every loop after the first, its features (see the MLP

@@ -58,9 +58,8 @@ def chebyshev_value(m: int, t):
 
 
 def chebyshev_sigmas(m: int, gamma_hat: float) -> np.ndarray:
-    """sigma_1..sigma_m of Alg. 2: sigma_1 = 1/gamma_hat (line 2 after
-    the scaling of line 1), sigma_{i+1} = 1 / (2/sigma_1 - sigma_i)
-    (line 6)."""
+    """sigma_1..sigma_m of Alg. 2: sigma_1 = 1/gamma_hat after the shift
+    and scale to (H - cI)/e, sigma_{i+1} = 1 / (2/sigma_1 - sigma_i)."""
     s = np.empty(m)
     s[0] = 1.0 / gamma_hat
     for i in range(1, m):
@@ -103,10 +102,10 @@ def lanczos_start(n: int, seed: int) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------
-# Alg. 1 line 3: Lanczos estimate of the spectral bounds
+# Alg. 1: Lanczos estimate of the spectral bounds
 # ----------------------------------------------------------------------
 def lanczos_bounds(H: np.ndarray, steps: int, v0: np.ndarray) -> dict:
-    """A few Lanczos steps (Alg. 1 line 3, Sec. 3.1 and footnote of
+    """A few Lanczos steps (Alg. 1, Sec. 3.1 and footnote of
     Sec. 3.2) with full reorthogonalisation (classical Gram-Schmidt,
     applied twice).  Returns beta = theta_max + ||f|| (reading R4), the
     smallest Ritz value theta_min and ||H||_est (R6)."""
@@ -159,7 +158,7 @@ def chebyshev_filter(H, Y0, degrees, lam1: float, c: float, e: float):
 
     Y0's columns are sorted by ascending degree (m_j >= 1).  Each column j
     of the result equals C_{m_j}(Hs) Y0_j / C_{m_j}(gamma_hat), Hs =
-    (H - cI)/e, gamma_hat = (lam1 - c)/e.  The scaling of line 1 is
+    (H - cI)/e, gamma_hat = (lam1 - c)/e.  The shift and scale are
     applied to each product rather than to H, so H is left untouched."""
     m = np.asarray(degrees, dtype=np.int64)
     k = Y0.shape[1]
@@ -168,34 +167,34 @@ def chebyshev_filter(H, Y0, degrees, lam1: float, c: float, e: float):
     if np.any(m < 1) or np.any(np.diff(m) < 0):
         raise ValueError("degrees must be >= 1 and ascending")
 
-    def hs(Y):  # line 1: (H - cI)/e applied to a block
+    def hs(Y):  # (H - cI)/e applied to a block
         return (H @ Y - c * Y) / e
 
-    sigma1 = e / (lam1 - c)  # line 2
+    sigma1 = e / (lam1 - c)
     sigma = sigma1
     y_prev = Y0
-    y_cur = sigma1 * hs(Y0)  # line 3
+    y_cur = sigma1 * hs(Y0)  # first degree: Y_1
     out = np.empty_like(Y0)
-    s = int(np.searchsorted(m, 1, side="right"))  # line 4: first m_j > 1
+    s = int(np.searchsorted(m, 1, side="right"))  # first column with m_j > 1
     out[:, :s] = y_cur[:, :s]
-    for i in range(1, int(m[-1])):  # line 5: builds Y_{i+1}
-        sigma_next = 1.0 / (2.0 / sigma1 - sigma)  # line 6
-        y_next = y_cur.copy()  # line 7: finished columns carried over
+    for i in range(1, int(m[-1])):  # builds Y_{i+1}
+        sigma_next = 1.0 / (2.0 / sigma1 - sigma)
+        y_next = y_cur.copy()  # finished columns carried over
         y_next[:, s:] = (2.0 * sigma_next * hs(y_cur[:, s:])
-                         - sigma_next * sigma * y_prev[:, s:])  # line 8 (R1)
+                         - sigma_next * sigma * y_prev[:, s:])  # reading R1
         y_prev, y_cur, sigma = y_cur, y_next, sigma_next
-        s_new = int(np.searchsorted(m, i + 1, side="right"))  # line 9
+        s_new = int(np.searchsorted(m, i + 1, side="right"))  # columns finished at degree i+1
         out[:, s:s_new] = y_cur[:, s:s_new]
         s = s_new
     return out
 
 
 # ----------------------------------------------------------------------
-# Alg. 1 line 6: orthonormalise [Y_locked, Y] (Householder QR)
+# Alg. 1, QR step: orthonormalise [Y_locked, Y] (Householder QR)
 # ----------------------------------------------------------------------
 def orthonormalize(Y, locked=None):
     """Householder QR (LAPACK zgeqrf via numpy) of [locked, Y], as in
-    Alg. 1 line 6 and Sec. 3.1.  Returns the columns of Q that belong to
+    Alg. 1 (QR step) and Sec. 3.1.  Returns the columns of Q that belong to
     Y, with phases fixed so that the corresponding diagonal of R is real
     and positive (which makes Q unique)."""
     nl = 0 if locked is None else locked.shape[1]
@@ -207,12 +206,12 @@ def orthonormalize(Y, locked=None):
 
 
 # ----------------------------------------------------------------------
-# Alg. 1 lines 7-9: Rayleigh-Ritz
+# Alg. 1: Rayleigh-Ritz
 # ----------------------------------------------------------------------
 def rayleigh_ritz(H, Q):
     """G = Q^H H Q (Hermitianised), G W = W Lambda by LAPACK's Hermitian
     eigensolver (ascending), Y = Q W; also returns H Y = (H Q) W
-    (Alg. 1 lines 7-9, Sec. 3.1)."""
+    (Alg. 1, Sec. 3.1)."""
     HQ = H @ Q
     G = Q.conj().T @ HQ
     G = 0.5 * (G + G.conj().T)
@@ -226,7 +225,7 @@ def residuals(HY, Y, lam, norm_h: float):
 
 
 # ----------------------------------------------------------------------
-# Alg. 1 line 10 (locking) and line 11 (degree optimisation)
+# Alg. 1: locking and degree optimisation
 # ----------------------------------------------------------------------
 def lock_mask(resid, n_wanted_left: int, tol: float):
     """Pairs to lock (reading R7): residual <= tol and ascending position

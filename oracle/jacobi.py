@@ -1,7 +1,7 @@
 """Cyclic Jacobi eigensolver for small complex Hermitian matrices.
 
 TEST INFRASTRUCTURE: a brute-force check of the Rayleigh-Ritz step's
-reduced eigenproblem (Alg. 1 line 8) and of the whole-solve results on
+reduced eigenproblem (Alg. 1) and of the whole-solve results on
 tiny matrices, independent of LAPACK.  Each rotation first removes the
 phase of a_pq and then applies the symmetric two-sided Jacobi rotation
 (Golub and Van Loan, Matrix Computations, Sec. 8.5).  Pure numpy, meant

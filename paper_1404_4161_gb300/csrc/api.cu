@@ -1,10 +1,9 @@
 // C ABI and solver core of the ChFSI library.
 //
 // Host-side orchestration of Algorithm 1 (ChFSI) of arXiv 1404.4161 over
-// device kernels: Lanczos bounds (line 3), the Chebyshev filter of
-// Algorithm 2 (line 5), orthonormalisation against the locked block (line
-// 6), Rayleigh-Ritz (lines 7-9), residuals, locking (line 10) and degree
-// optimisation (line 11).  Every arithmetic step runs in this library's
+// device kernels: Lanczos bounds of the spectrum, the Chebyshev filter of
+// Algorithm 2, orthonormalisation against the locked block, Rayleigh-Ritz,
+// residuals, locking and degree optimisation.  Every arithmetic step runs in this library's
 // kernels; the k x k Cholesky, triangular inverse and Hermitian
 // eigensolve of the reduced problems use cuSOLVER.  The host only reads a
 // small control block per loop (converged count, interval, sorted degrees)
@@ -312,7 +311,7 @@ void gemm_nn(chfsi_ctx* ctx, int M, int N, int K, const double2* A, int lda, con
 }
 
 // ------------------------------------------------- orthonormalisation ----
-// Alg. 1 line 6 on the device: two block Gram-Schmidt passes against the
+// The QR step of Alg. 1 on the device: two block Gram-Schmidt passes against the
 // locked block, column normalisation, then CholQR2 (a shifted Cholesky QR
 // pass first when the Gram matrix is not numerically positive definite).
 void orthonormalize_dev(chfsi_ctx* ctx, int n, int nl, const double2* L, int k, double2* Y,
@@ -506,7 +505,7 @@ struct Problem {
       throw ChfsiError{CHFSI_ENAN, "NaN/Inf in the starting block"};
     if (any_nonfinite(ctx, (size_t)2 * n * n, (const double*)H))
       throw ChfsiError{CHFSI_ENAN, "NaN/Inf in H"};
-    // Alg. 1 line 3: bounds of the spectrum.
+    // Alg. 1: bounds of the spectrum (Lanczos, Sec. 3.1).
     lanczos_dev(ctx, H, n, o->lanczos_steps, o->seed, bnd);
     CHFSI_CUDA_TRY(cudaMemcpyAsync(bnd_h, bnd, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
     mark(1);

@@ -1,9 +1,9 @@
 // FP64 complex dense kernels of the ChFSI path: the NN product with the
 // fused three-term-recurrence epilogue (the FP64 Chebyshev filter step of
-// Alg. 2 line 8, and H*Q of the Rayleigh-Ritz step, Alg. 1 line 7), the
+// Alg. 2, and H*Q of the Rayleigh-Ritz step of Alg. 1), the
 // split-K conjugate-transpose product for the tall-skinny Gram and
-// projection matrices (Alg. 1 lines 6-7), the Hermitian mat-vec of the
-// Lanczos step (Alg. 1 line 3), and the column reductions for residuals.
+// projection matrices (QR and Rayleigh-Ritz of Alg. 1), the Hermitian mat-vec of the
+// Lanczos bounds (Alg. 1, Sec. 3.1), and the column reductions for residuals.
 //
 // GB300 runs FP64 on a narrow pipe (about 1.1 TFLOP/s for the whole GPU),
 // so these kernels are bound by DFMA issue at any practical size: a 32 x 32

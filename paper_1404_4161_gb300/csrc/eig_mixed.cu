@@ -1,4 +1,4 @@
-// Reduced Hermitian eigensolve of the Rayleigh-Ritz step (Alg. 1 line 8,
+// Reduced Hermitian eigensolve of the Rayleigh-Ritz step (Alg. 1,
 // G W = W Lambda for the k x k Rayleigh quotient) in mixed precision.
 //
 // GB300's FP64 pipe makes LAPACK-style k x k eigensolvers slow (about

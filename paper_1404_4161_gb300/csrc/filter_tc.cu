@@ -1,7 +1,7 @@
 // Split-precision Chebyshev filter on the GB300 tensor cores (tcgen05 +
 // TMEM + TMA), sm_103a.
 //
-// Each step of Alg. 2 (line 8) computes Y_{i+1} = a_i (H Y_i - c Y_i) +
+// Each step of the Alg. 2 recurrence computes Y_{i+1} = a_i (H Y_i - c Y_i) +
 // b_i Y_{i-1} on the active (still unfinished) suffix of the degree-sorted
 // block.  The complex product is one real GEMM
 //

@@ -2,7 +2,7 @@
 //
 // GB300 issues FP64 on a narrow pipe (~1.1 TFLOP/s), while its BF16 tensor
 // cores run ~1.9 PFLOP/s.  This kernel computes the FP64 products of the
-// Rayleigh-Ritz step (Z = H Q, Alg. 1 line 7) to ~2^-43 accuracy with
+// Rayleigh-Ritz step (Z = H Q, Alg. 1) to ~2^-43 accuracy with
 // error-free splitting (Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59,
 // 2012): every operand row (A) and column (B) is scaled by a power of two
 // to [-1, 1] and cut into S slices of 7-bit signed digits (S = 7 for the

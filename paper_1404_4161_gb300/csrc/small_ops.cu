@@ -1,7 +1,7 @@
 // Loop control of Alg. 1 on the device: locking of converged pairs
-// (Alg. 1 line 10, out-of-order locking of Sec. 4), the update of the
+// (Alg. 1, out-of-order locking of Sec. 4), the update of the
 // filter interval (alpha, gamma; Sec. 3.2 and its footnote), the analytic
-// degree rule (Alg. 1 line 11, Single Optimization of Sec. 3.2) and the
+// degree rule (Alg. 1, Single Optimization of Sec. 3.2) and the
 // stable ascending sort of the columns by degree (Sec. 4), so the filter
 // can run on a shrinking suffix of the block.  All of it is O(k) or O(k^2)
 // work on at most a few thousand values: one CTA per kernel.

@@ -81,9 +81,9 @@ def test_solve_batched_sequences():
     every step has its problem's known spectrum), two steps, solved in
     lockstep with one batched filter launch per loop."""
     from paper_1404_4161_gb300.build import build
-    from workloads.synthetic import BASE_SEED, CONFIGS, config_sequence
+    from workloads.synthetic import BASE_SEED, WORKLOADS, config_sequence
     build()
-    cfg = CONFIGS[4]
+    cfg = WORKLOADS["batched64"]
     sizes = [(320, 20, 5), (448, 28, 7), (512, 32, 8), (600, 37, 9), (384, 24, 6), (700, 43, 10)]
     seqs, ref = [], []
     for i, (n, nev, nex) in enumerate(sizes):

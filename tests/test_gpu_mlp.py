@@ -17,7 +17,7 @@ from paper_1404_4161_gb300 import _lib as L
 from paper_1404_4161_gb300 import learned
 from paper_1404_4161_gb300.solver import Chfsi, colmajor
 from tests.gpu_util import DEV, from_dev_cm, to_dev_cm
-from workloads.synthetic import BASE_SEED, CONFIGS, config_sequence, random_block
+from workloads.synthetic import BASE_SEED, WORKLOADS, config_sequence, random_block
 
 pytestmark = pytest.mark.gpu
 
@@ -98,7 +98,7 @@ def test_learned_degrees_ab():
     extra loop over the continuation; the gains are printed."""
     from paper_1404_4161_gb300.build import build
     build()
-    cfg = CONFIGS[5]
+    cfg = WORKLOADS["seq30_n8192"]
     n, nev, nex = 1024, 64, 16
     Hs, lam = config_sequence(cfg, BASE_SEED + 5000, length=30, n=n)
     Hc = [to_dev_cm(h) for h in Hs]

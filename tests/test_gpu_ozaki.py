@@ -16,7 +16,7 @@ import oracle
 from paper_1404_4161_gb300 import _lib as L
 from paper_1404_4161_gb300.solver import Chfsi, colmajor
 from tests.gpu_util import DEV, from_dev_cm, known_problem, to_dev_cm
-from workloads.synthetic import BASE_SEED, CONFIGS, config_problem, config_sequence, random_block
+from workloads.synthetic import BASE_SEED, WORKLOADS, config_problem, config_sequence, random_block
 
 pytestmark = pytest.mark.gpu
 
@@ -116,7 +116,7 @@ def test_dfma_engine_same_entry(ctx):
 def test_solve_with_tensor_core_fp64_products():
     from paper_1404_4161_gb300.build import build
     build()
-    cfg = CONFIGS[1]
+    cfg = WORKLOADS["single_n512"]
     H, lam = config_problem(cfg, BASE_SEED + 1000)
     X0 = random_block(cfg.n, cfg.nev + cfg.nex, BASE_SEED + 1500)
     s = Chfsi(precision=L.PREC_TC, f64_gemm=L.GEMM_OZAKI)
@@ -132,7 +132,7 @@ def test_solve_with_tensor_core_fp64_products():
     # X^H X = I to 1e-13 k (the Gram and R^-1 products carry ~1e-12)
     assert np.abs(X.conj().T @ X - np.eye(X.shape[1])).max() < 1e-13 * X.shape[1]
     # a correlated sequence with the exact spectrum kept (delta = 0)
-    cfg2 = CONFIGS[2]
+    cfg2 = WORKLOADS["seq10_n4096"]
     n, nev, nex = 1024, 64, 16
     Hs, lam2 = config_sequence(cfg2, BASE_SEED + 2000, length=3, n=n, delta=0.0)
     Xc = to_dev_cm(random_block(n, nev + nex, BASE_SEED + 2500))
@@ -175,7 +175,7 @@ def test_sequence_warm_rayleigh_ritz():
     same eigenpairs, fewer loops than without it."""
     from paper_1404_4161_gb300.build import build
     build()
-    cfg2 = CONFIGS[2]
+    cfg2 = WORKLOADS["seq10_n4096"]
     n, nev, nex = 1024, 64, 16
     Hs, lam2 = config_sequence(cfg2, BASE_SEED + 2200, length=4, n=n, delta=0.0)
     loops = {}

@@ -12,7 +12,7 @@ import oracle
 from paper_1404_4161_gb300 import _lib as L
 from paper_1404_4161_gb300.solver import Chfsi
 from tests.gpu_util import DEV, from_dev_cm, known_problem, to_dev_cm
-from workloads.synthetic import (BASE_SEED, CONFIGS, config_problem, config_sequence,
+from workloads.synthetic import (BASE_SEED, WORKLOADS, config_problem, config_sequence,
                                  random_block)
 
 pytestmark = pytest.mark.gpu
@@ -42,7 +42,7 @@ def check(H, lam, X, ev, nev, tol=1e-10):
 
 
 def test_solve_config1(ctx):
-    cfg = CONFIGS[1]
+    cfg = WORKLOADS["single_n512"]
     H, lam = config_problem(cfg, BASE_SEED + 1000)
     X0 = random_block(cfg.n, cfg.nev + cfg.nex, BASE_SEED + 1500)
     ref = oracle.chfsi(H, cfg.nev, cfg.nex, X0, cfg.tol)
@@ -61,7 +61,7 @@ def test_solve_config1(ctx):
 
 
 def test_sequence_known_spectrum(ctx):
-    cfg = CONFIGS[2]
+    cfg = WORKLOADS["seq10_n4096"]
     n, nev, nex = 512, 32, 8
     Hs, lam = config_sequence(cfg, BASE_SEED + 2000, length=3, n=n, delta=0.0)
     X0 = random_block(n, nev + nex, BASE_SEED + 2500)
@@ -79,7 +79,7 @@ def test_sequence_known_spectrum(ctx):
 
 
 def test_sequence_host_buffers_match_device(ctx):
-    cfg = CONFIGS[2]
+    cfg = WORKLOADS["seq10_n4096"]
     n, nev, nex = 384, 16, 8
     Hs, lam = config_sequence(cfg, BASE_SEED + 2100, length=2, n=n)
     X0 = random_block(n, nev + nex, BASE_SEED + 2600)

@@ -18,7 +18,7 @@ import oracle
 from paper_1404_4161_gb300 import _lib as L
 from paper_1404_4161_gb300.solver import Chfsi
 from tests.gpu_util import DEV, colrel, from_dev_cm, known_problem, to_dev_cm
-from workloads.synthetic import BASE_SEED, CONFIGS, config_problem, config_sequence, random_block
+from workloads.synthetic import BASE_SEED, WORKLOADS, config_problem, config_sequence, random_block
 
 pytestmark = pytest.mark.gpu
 U16 = 2.0 ** -16
@@ -100,7 +100,7 @@ def check(H, lam, X, ev, nev, tol=1e-10):
 def test_solve_config1_tensor_core(prec):
     from paper_1404_4161_gb300.build import build
     build()
-    cfg = CONFIGS[1]
+    cfg = WORKLOADS["single_n512"]
     H, lam = config_problem(cfg, BASE_SEED + 1000)
     X0 = random_block(cfg.n, cfg.nev + cfg.nex, BASE_SEED + 1500)
     s = Chfsi(precision=prec)
@@ -114,7 +114,7 @@ def test_solve_config1_tensor_core(prec):
 
 
 def test_sequence_tensor_core_known_spectrum():
-    cfg = CONFIGS[2]
+    cfg = WORKLOADS["seq10_n4096"]
     n, nev, nex = 768, 48, 12
     Hs, lam = config_sequence(cfg, BASE_SEED + 2000, length=3, n=n, delta=0.0)
     X0 = random_block(n, nev + nex, BASE_SEED + 2500)

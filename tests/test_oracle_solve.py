@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
-from workloads.synthetic import (CONFIGS, BASE_SEED, config_problem, config_sequence,
+from workloads.synthetic import (WORKLOADS, BASE_SEED, config_problem, config_sequence,
                                  haar_unitary, hermitian_from_spectrum, random_block)
 
 
@@ -30,7 +30,7 @@ def check_solution(H, lam_true, res, nev, tol):
 
 
 def test_solve_config1_known_spectrum():
-    cfg = CONFIGS[1]
+    cfg = WORKLOADS["single_n512"]
     H, lam = config_problem(cfg, BASE_SEED + 1000)
     X0 = random_block(cfg.n, cfg.nev + cfg.nex, BASE_SEED + 1500)
     res = oracle.chfsi(H, cfg.nev, cfg.nex, X0, cfg.tol, deg_max=cfg.deg_max)
@@ -56,7 +56,7 @@ def test_solve_tiny_vs_jacobi():
 def test_sequence_known_spectrum_and_warm_start_gain():
     """delta = 0 keeps every problem's spectrum exact; warm starts need
     less filtering than random starts (Sec. 5.2, Fig. 2b: >2x)."""
-    cfg = CONFIGS[2]
+    cfg = WORKLOADS["seq10_n4096"]
     n, nev, nex = 512, 32, 8
     Hs, lam = config_sequence(cfg, BASE_SEED + 2000, length=3, n=n, delta=0.0)
     X0 = random_block(n, nev + nex, BASE_SEED + 2500)
@@ -72,7 +72,7 @@ def test_sequence_known_spectrum_and_warm_start_gain():
 def test_single_optimization_saves_work():
     """Per-vector degrees need fewer matrix-vector products than one
     uniform degree for the same tolerance (Sec. 5.2, Fig. 5a)."""
-    cfg = CONFIGS[1]
+    cfg = WORKLOADS["single_n512"]
     H, lam = config_problem(cfg, BASE_SEED + 1000)
     X0 = random_block(cfg.n, 48, BASE_SEED + 1500)
     opt = oracle.chfsi(H, 32, 16, X0, 1e-10)

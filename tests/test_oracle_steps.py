@@ -1,5 +1,5 @@
 """Pins for the oracle's Lanczos bounds, QR, Rayleigh-Ritz, residuals,
-locking and degree rule (Alg. 1 lines 3, 6-11; Sec. 3.2)."""
+locking and degree rule (Alg. 1; Sec. 3.2)."""
 import math
 import os
 
@@ -20,7 +20,7 @@ def known(n, seed, lo=(-3.0, -1.0), bulk=(0.0, 20.0), n_low=None):
     return hermitian_from_spectrum(lam, q), lam, q
 
 
-# -------------------------- Lanczos (Alg. 1 line 3) ------------------------
+# -------------------------- Lanczos (Alg. 1) --------------------------------
 @pytest.mark.parametrize("n,seed", [(64, 1), (200, 2), (513, 3)])
 def test_lanczos_bounds_enclose_spectrum(n, seed):
     H, lam, _ = known(n, seed)
@@ -41,7 +41,7 @@ def test_lanczos_full_krylov_space_is_exact():
     assert abs(b["theta_max"] - lam[-1]) < 1e-10
 
 
-# -------------------------- QR (Alg. 1 line 6) ------------------------------
+# -------------------------- QR (Alg. 1) -------------------------------------
 def gram_schmidt(A):
     """Brute-force modified Gram-Schmidt with positive real R diagonal."""
     A = A.copy()
@@ -76,7 +76,7 @@ def test_qr_against_locked():
     assert np.allclose(Q, gram_schmidt(np.concatenate([L, Y], 1))[:, 5:], atol=1e-12)
 
 
-# -------------------------- Rayleigh-Ritz (lines 7-9) -----------------------
+# -------------------------- Rayleigh-Ritz (Alg. 1) --------------------------
 def test_rr_exact_eigenvectors_give_exact_eigenvalues():
     H, lam, q = known(40, 7)
     lam_r, Y, HY = oracle.rayleigh_ritz(H, q[:, :6])

@@ -14,7 +14,7 @@ next (Sec. 2.2, Definitions 1 and 2).
 """
 from .synthetic import (  # noqa: F401
     BASE_SEED,
-    CONFIGS,
+    WORKLOADS,
     haar_unitary,
     two_band_spectrum,
     hermitian_from_spectrum,

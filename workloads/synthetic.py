@@ -46,16 +46,16 @@ class Config:
 # The five workloads of the hot path.  n_low follows the stated split
 # (40 for the n=512 problem, 300 for the n=4096 sequence) and otherwise
 # nev + nex//2.
-CONFIGS = {
-    1: Config("single_n512", 512, 32, 16, 40, (-2.0, -1.0), (0.0, 10.0)),
-    2: Config("seq10_n4096", 4096, 256, 64, 300, (-3.0, -1.0), (0.0, 20.0),
+WORKLOADS = {
+    "single_n512": Config("single_n512", 512, 32, 16, 40, (-2.0, -1.0), (0.0, 10.0)),
+    "seq10_n4096": Config("seq10_n4096", 4096, 256, 64, 300, (-3.0, -1.0), (0.0, 20.0),
               length=10, eps=1e-3, delta=1e-4),
-    3: Config("seq20_n13000", 13000, 800, 200, 900, (-5.0, -1.0), (0.0, 40.0),
+    "seq20_n13000": Config("seq20_n13000", 13000, 800, 200, 900, (-5.0, -1.0), (0.0, 40.0),
               length=20, eps=1e-3, delta=1e-4),
-    4: Config("batched64", 0, 0, 0, 0, (-3.0, -1.0), (0.0, 20.0),
+    "batched64": Config("batched64", 0, 0, 0, 0, (-3.0, -1.0), (0.0, 20.0),
               length=10, eps=1e-3, delta=1e-4,
               extra={"problems": 64, "n_range": (1500, 6000)}),
-    5: Config("seq30_n8192", 8192, 512, 128, 576, (-3.0, -1.0), (0.0, 20.0),
+    "seq30_n8192": Config("seq30_n8192", 8192, 512, 128, 576, (-3.0, -1.0), (0.0, 20.0),
               length=30, eps=1e-3, delta=1e-4),
 }
 
