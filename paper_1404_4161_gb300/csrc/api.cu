@@ -130,42 +130,6 @@ inline const double2* C2(const double* p) { return reinterpret_cast<const double
 
 // ------------------------------------------------------------ Lanczos ----
 // out4_dev = {beta, theta_min, theta_max, norm_h} (device).
-void lanczos_dev(chfsi_ctx* ctx, const double2* H, int n, int steps,
-                 unsigned long long seed, double* out4_dev) {
-  cudaStream_t st = ctx->stream;
-  const int m = std::min(steps, n);
-  double2* V = (double2*)ws_get(ctx, "lz_V", sizeof(double2) * (size_t)n * (m + 1));
-  double2* w = (double2*)ws_get(ctx, "lz_w", sizeof(double2) * (size_t)n);
-  double2* h1 = (double2*)ws_get(ctx, "lz_h1", sizeof(double2) * (m + 1));
-  double2* h2 = (double2*)ws_get(ctx, "lz_h2", sizeof(double2) * (m + 1));
-  double* ab = (double*)ws_get(ctx, "lz_ab", sizeof(double) * (2 * m + 2));
-  double* a = ab;
-  double* b = ab + m + 1;
-  lanczos_start_vec(st, n, seed, w);
-  vec_norm(st, n, w, b + m);
-  vec_scale_inv(st, n, w, b + m, V);
-  for (int j = 0; j < m; ++j) {
-    zhemv_cols(st, n, H, V + (size_t)j * n, w);
-    const double2* hh[2] = {h1, h2};
-    for (int pass = 0; pass < 2; ++pass) {
-      double2* h = const_cast<double2*>(hh[pass]);
-      zgemm_cn(ctx, j + 1, 1, n, V, n, w, n, h, j + 1);
-      EpiNN ep;
-      ep.alpha = -1.0;
-      ep.beta = 1.0;
-      ep.P = w;
-      ep.ldp = n;
-      ep.D = w;
-      ep.ldd = n;
-      zgemm_nn(st, n, 1, j + 1, V, n, h, j + 1, ep);
-    }
-    lanczos_alpha(st, j, h1, h2, a);
-    vec_norm(st, n, w, b + j);
-    vec_scale_inv(st, n, w, b + j, V + (size_t)(j + 1) * n);
-  }
-  tridiag_bounds(st, m, a, b, out4_dev);
-}
-
 // ------------------------------------------------------- FP64 filter ----
 void filter_f64(chfsi_ctx* ctx, const double2* H, int n, int k, const double2* Y0,
                 const int* deg, double lam1, double c, double e, double2* Yout) {
@@ -228,39 +192,6 @@ int read_info(chfsi_ctx* ctx) {
   return *h;
 }
 
-// Upper Cholesky factor of G (k x k) in place; returns LAPACK-style info.
-int potrf_upper(chfsi_ctx* ctx, int k, double2* G) {
-  int lwork = 0;
-  CHFSI_SOLVER_TRY(cusolverDnZpotrf_bufferSize(ctx->solver, CUBLAS_FILL_MODE_UPPER, k,
-                                               (cuDoubleComplex*)G, k, &lwork));
-  void* work = ws_get(ctx, "potrf_work", sizeof(cuDoubleComplex) * (size_t)std::max(lwork, 1));
-  const int slot = kt_begin(ctx->stream);
-  CHFSI_SOLVER_TRY(cusolverDnZpotrf(ctx->solver, CUBLAS_FILL_MODE_UPPER, k,
-                                    (cuDoubleComplex*)G, k, (cuDoubleComplex*)work, lwork,
-                                    dev_info(ctx)));
-  kt_end(ctx->stream, slot, KT_SOLVER, 0.0);
-  return read_info(ctx);
-}
-
-// Inverse of the upper triangular R (k x k) in place, strict lower part zeroed.
-void trtri_upper(chfsi_ctx* ctx, int k, double2* R) {
-  zero_strict_lower(ctx->stream, k, R, k);
-  size_t dbytes = 0, hbytes = 0;
-  CHFSI_SOLVER_TRY(cusolverDnXtrtri_bufferSize(ctx->solver, CUBLAS_FILL_MODE_UPPER,
-                                               CUBLAS_DIAG_NON_UNIT, k, CUDA_C_64F, R, k,
-                                               &dbytes, &hbytes));
-  void* dwork = ws_get(ctx, "trtri_work", std::max<size_t>(dbytes, 16));
-  std::vector<char> hwork(std::max<size_t>(hbytes, 16));
-  const int slot = kt_begin(ctx->stream);
-  CHFSI_SOLVER_TRY(cusolverDnXtrtri(ctx->solver, CUBLAS_FILL_MODE_UPPER, CUBLAS_DIAG_NON_UNIT,
-                                    k, CUDA_C_64F, R, k, dwork, dbytes, hwork.data(), hbytes,
-                                    dev_info(ctx)));
-  kt_end(ctx->stream, slot, KT_SOLVER, 0.0);
-  const int info = read_info(ctx);
-  if (info != 0)
-    throw ChfsiError{CHFSI_EBREAKDOWN, "triangular inverse: singular R (info " +
-                                           std::to_string(info) + ")"};
-}
 
 // Hermitian eigensolve of G (k x k, lower part read): eigenvectors overwrite G.
 void heevd(chfsi_ctx* ctx, int k, double2* G, double* w) {
@@ -340,7 +271,7 @@ void orthonormalize_dev(chfsi_ctx* ctx, int n, int nl, const double2* L, int k, 
       cholqr_shift(st, n, k, G, k, shift);
       add_diag(st, k, G, k, shift);
     }
-    int info = potrf_upper(ctx, k, G);
+    int info = cholinv_upper(ctx, k, G);  // G <- R^{-1}, R^H R = G
     if (info != 0) {
       if (pass == 0 && !shifted) {
         shifted = true;
@@ -351,7 +282,6 @@ void orthonormalize_dev(chfsi_ctx* ctx, int n, int nl, const double2* L, int k, 
       throw ChfsiError{CHFSI_EBREAKDOWN, "CholQR: Gram matrix not positive definite (info " +
                                              std::to_string(info) + ")"};
     }
-    trtri_upper(ctx, k, G);
     gemm_nn(ctx, n, k, k, Y, n, G, k, T, n);
     CHFSI_CUDA_TRY(cudaMemcpyAsync(Y, T, sizeof(double2) * (size_t)n * k,
                                    cudaMemcpyDeviceToDevice, st));
@@ -508,8 +438,14 @@ struct Problem {
     // Alg. 1: bounds of the spectrum (Lanczos, Sec. 3.1).
     lanczos_dev(ctx, H, n, o->lanczos_steps, o->seed, bnd);
     CHFSI_CUDA_TRY(cudaMemcpyAsync(bnd_h, bnd, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
+    int* lz_err_h = (int*)(hp + 640);
+    CHFSI_CUDA_TRY(cudaMemcpyAsync(lz_err_h, lanczos_error_word(ctx), sizeof(int),
+                                   cudaMemcpyDeviceToHost, st));
     mark(1);
     CHFSI_CUDA_TRY(cudaStreamSynchronize(st));
+    if (*lz_err_h)
+      throw ChfsiError{CHFSI_ETIMEOUT, "Lanczos: a bounded grid barrier gave up (code " +
+                                           std::to_string(*lz_err_h) + ")"};
     S.ms_lanczos = ms(0, 1);
     beta = bnd_h[0];
     norm_h = bnd_h[3];
@@ -1071,9 +1007,15 @@ int chfsi_lanczos(chfsi_ctx* ctx, const double* H, int n, int steps, unsigned lo
     CHFSI_REQUIRE(H && out_host && n >= 1 && steps >= 2, "bad Lanczos arguments");
     double* d = (double*)ws_get(ctx, "api_bnd", sizeof(double) * 4);
     lanczos_dev(ctx, C2(H), n, steps, seed, d);
+    int* err_h = (int*)pinned_get(ctx, 64);
     CHFSI_CUDA_TRY(cudaMemcpyAsync(out_host, d, sizeof(double) * 4, cudaMemcpyDeviceToHost,
                                    ctx->stream));
+    CHFSI_CUDA_TRY(cudaMemcpyAsync(err_h, lanczos_error_word(ctx), sizeof(int),
+                                   cudaMemcpyDeviceToHost, ctx->stream));
     CHFSI_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    if (*err_h)
+      throw ChfsiError{CHFSI_ETIMEOUT, "Lanczos: a bounded grid barrier gave up (code " +
+                                           std::to_string(*err_h) + ")"};
   });
 }
 

@@ -138,11 +138,8 @@ void zgemm_cn(chfsi_ctx* ctx, int K1, int K2, int Nr, const double2* A, int lda,
               const double2* B, int ldb, double2* C, int ldc, double alpha = 1.0,
               double beta = 0.0);
 
-// y = H x for Hermitian H (n x n): uses H x = H^H x, one warp per entry.
-void zhemv_cols(cudaStream_t st, int n, const double2* H, const double2* x, double2* y);
 
 void hermitianize(cudaStream_t st, int k, double2* G, int ldg);
-void zero_strict_lower(cudaStream_t st, int k, double2* R, int ldr);
 void add_diag(cudaStream_t st, int k, double2* G, int ldg, const double* shift_dev);
 void column_norms(cudaStream_t st, int n, int k, const double2* Y, int ldy, double* out);
 void scale_columns_inv(cudaStream_t st, int n, int k, double2* Y, int ldy, const double* norms);
@@ -160,13 +157,17 @@ int any_nonfinite(chfsi_ctx* ctx, size_t count, const double* v);
 double deviation_from_identity(chfsi_ctx* ctx, int k, const double2* G);
 void ns_matrix(cudaStream_t st, int k, const double2* G, double2* T);
 
-// Lanczos helpers.
-void lanczos_start_vec(cudaStream_t st, int n, unsigned long long seed, double2* v);
-void vec_norm(cudaStream_t st, int n, const double2* v, double* out);
-void vec_scale_inv(cudaStream_t st, int n, const double2* w, const double* nrm, double2* v);
-void lanczos_alpha(cudaStream_t st, int j, const double2* h1, const double2* h2, double* alpha);
-void tridiag_bounds(cudaStream_t st, int m, const double* alpha, const double* beta,
-                    double* out4);
+// Lanczos bounds of the spectrum (lanczos.cu): out4_dev = {theta_max +
+// beta_m, theta_min, theta_max, max|theta|}; NaN when a bounded wait of the
+// persistent kernel gave up, with the code in *lanczos_error_word(ctx).
+void lanczos_dev(chfsi_ctx* ctx, const double2* H, int n, int steps, unsigned long long seed,
+                 double* out4_dev);
+const int* lanczos_error_word(chfsi_ctx* ctx);
+
+// W = R^{-1} in place for the Hermitian positive definite G = R^H R (k x k,
+// ld k; cholinv.cu).  Returns 0 or the order of the first leading minor
+// that is not positive definite (W then incomplete); synchronises.
+int cholinv_upper(chfsi_ctx* ctx, int k, double2* G);
 
 // Loop control: locking, interval update, degrees, sorting (small_ops.cu).
 struct LoopCtl {

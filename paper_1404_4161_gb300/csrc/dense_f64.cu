@@ -170,22 +170,6 @@ __global__ void zgemm_cn_reduce_kernel(int K1, int K2, int splits, const double2
 }
 
 // y[r] = sum_j conj(H[j, r]) x[j]  (= (H x)[r] for Hermitian H).
-__global__ void zhemv_cols_kernel(int n, const double2* __restrict__ H,
-                                  const double2* __restrict__ x, double2* __restrict__ y) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= n) return;
-  const double2* col = H + (size_t)warp * n;
-  double2 s = make_double2(0.0, 0.0);
-  for (int j = lane; j < n; j += 32) cmac_conj(s, col[j], x[j]);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-    s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
-  }
-  if (lane == 0) y[warp] = s;
-}
-
 template <int NT>
 __device__ double block_sum(double v, double* sh) {
 #pragma unroll
@@ -254,11 +238,6 @@ __global__ void hermitianize_kernel(int k, double2* G, int ldg) {
   G[j + (size_t)i * ldg] = make_double2(v.x, -v.y);
 }
 
-__global__ void zero_strict_lower_kernel(int k, double2* R, int ldr) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y;
-  if (i < k && i > j) R[i + (size_t)j * ldr] = make_double2(0.0, 0.0);
-}
 
 __global__ void add_diag_kernel(int k, double2* G, int ldg, const double* shift) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -297,104 +276,6 @@ __global__ void nonfinite_kernel(size_t count, const double* v, int* flag) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
        i += (size_t)gridDim.x * blockDim.x)
     if (!isfinite(v[i])) *flag = 1;
-}
-
-// ---- Lanczos pieces ------------------------------------------------------
-__device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed,
-                                                            unsigned long long t) {
-  unsigned long long z = seed + (t + 1ull) * 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
-__global__ void lanczos_start_kernel(int n, unsigned long long seed, double2* v) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  const double sc = 1.1102230246251565e-16;  // 2^-53
-  const unsigned long long a = splitmix64_at(seed, 2ull * j) >> 11;
-  const unsigned long long b = splitmix64_at(seed, 2ull * j + 1ull) >> 11;
-  v[j] = make_double2((double)a * sc * 2.0 - 1.0, (double)b * sc * 2.0 - 1.0);
-}
-
-__global__ void __launch_bounds__(1024) vec_norm_kernel(int n, const double2* v, double* out) {
-  __shared__ double sh[32];
-  double s = 0.0;
-  for (int r = threadIdx.x; r < n; r += 1024) s += v[r].x * v[r].x + v[r].y * v[r].y;
-  s = block_sum<1024>(s, sh);
-  if (threadIdx.x == 0) *out = sqrt(s);
-}
-
-__global__ void vec_scale_inv_kernel(int n, const double2* w, const double* nrm, double2* v) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  const double inv = 1.0 / *nrm;
-  v[r] = make_double2(w[r].x * inv, w[r].y * inv);
-}
-
-__global__ void lanczos_alpha_kernel(int j, const double2* h1, const double2* h2,
-                                     double* alpha) {
-  alpha[j] = h1[j].x + h2[j].x;
-}
-
-// Number of eigenvalues of the symmetric tridiagonal (a, b) below x
-// (Sturm sequence count with the LDL^T pivots).
-__device__ int sturm_count(int m, const double* a, const double* b, double x) {
-  int cnt = 0;
-  double d = 1.0;
-  for (int i = 0; i < m; ++i) {
-    const double bb = (i > 0) ? b[i - 1] * b[i - 1] : 0.0;
-    d = (a[i] - x) - ((i > 0) ? bb / d : 0.0);
-    if (d == 0.0) d = -1e-300;
-    if (d < 0.0) ++cnt;
-  }
-  return cnt;
-}
-
-// Extreme eigenvalues of the Lanczos tridiagonal by multisection on Sturm
-// counts: one warp, each round splits the bracket into 33 parts and keeps
-// the part holding the wanted eigenvalue (5 bits per round instead of 1).
-// out4 = {theta_max + beta_m, theta_min, theta_max, max|theta|}, beta_m the
-// norm of the last residual vector.
-__global__ void tridiag_bounds_kernel(int m_in, const double* a, const double* b, double* out) {
-  const int lane = threadIdx.x & 31;
-  // Steps after an (almost) invariant Krylov space are not used: the
-  // recurrence stops at the first beta_j <= 1e-14 max(|alpha_j|, 1).
-  int m = m_in;
-  for (int j = 0; j < m_in; ++j)
-    if (!(b[j] > 1e-14 * fmax(fabs(a[j]), 1.0))) { m = j + 1; break; }
-  double lo = a[0], hi = a[0];
-  for (int i = 0; i < m; ++i) {
-    const double r = ((i > 0) ? fabs(b[i - 1]) : 0.0) + ((i < m - 1) ? fabs(b[i]) : 0.0);
-    lo = fmin(lo, a[i] - r);
-    hi = fmax(hi, a[i] + r);
-  }
-  double th[2];
-  for (int which = 0; which < 2; ++which) {
-    const int target = which == 0 ? 1 : m;  // smallest x with count(x) >= target
-    double l = lo - 1e-12 * fabs(lo) - 1e-300, h = hi + 1e-12 * fabs(hi) + 1e-300;
-    for (int it = 0; it < 40; ++it) {
-      const double step = (h - l) / 33.0;
-      const double x = l + step * (lane + 1);
-      const bool ge = sturm_count(m, a, b, x) >= target;
-      const unsigned mask = __ballot_sync(0xffffffffu, ge);
-      // first lane whose point has count >= target: new bracket (x_{f-1}, x_f]
-      const int f = mask ? __ffs(mask) - 1 : 32;
-      const double nl = l + step * f;
-      const double nh = (f < 32) ? l + step * (f + 1) : h;
-      if (!(nl < nh) || (nl == l && nh == h)) break;
-      l = nl;
-      h = nh;
-      if (h - l <= 4e-16 * fmax(fabs(l), fabs(h))) break;
-    }
-    th[which] = 0.5 * (l + h);
-  }
-  if (lane == 0) {
-    out[1] = th[0];
-    out[2] = th[1];
-    out[0] = th[1] + b[m - 1];
-    out[3] = fmax(fabs(th[0]), fabs(th[1]));
-  }
 }
 
 __global__ void residual_block_kernel(int n, const double2* __restrict__ HY,
@@ -455,10 +336,6 @@ void zgemm_cn(chfsi_ctx* ctx, int K1, int K2, int Nr, const double2* A, int lda,
   chfsi_check_launch("zgemm_cn_reduce");
 }
 
-void zhemv_cols(cudaStream_t st, int n, const double2* H, const double2* x, double2* y) {
-  zhemv_cols_kernel<<<(n + 7) / 8, 256, 0, st>>>(n, H, x, y);
-  chfsi_check_launch("zhemv_cols");
-}
 
 void hermitianize(cudaStream_t st, int k, double2* G, int ldg) {
   if (k <= 0) return;
@@ -466,11 +343,6 @@ void hermitianize(cudaStream_t st, int k, double2* G, int ldg) {
   chfsi_check_launch("hermitianize");
 }
 
-void zero_strict_lower(cudaStream_t st, int k, double2* R, int ldr) {
-  if (k <= 0) return;
-  zero_strict_lower_kernel<<<dim3((k + 127) / 128, k), 128, 0, st>>>(k, R, ldr);
-  chfsi_check_launch("zero_strict_lower");
-}
 
 void add_diag(cudaStream_t st, int k, double2* G, int ldg, const double* shift_dev) {
   add_diag_kernel<<<(k + 255) / 256, 256, 0, st>>>(k, G, ldg, shift_dev);
@@ -532,32 +404,10 @@ int any_nonfinite(chfsi_ctx* ctx, size_t count, const double* v) {
   return *h;
 }
 
-void lanczos_start_vec(cudaStream_t st, int n, unsigned long long seed, double2* v) {
-  lanczos_start_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, seed, v);
-  chfsi_check_launch("lanczos_start");
-}
 
-void vec_norm(cudaStream_t st, int n, const double2* v, double* out) {
-  vec_norm_kernel<<<1, 1024, 0, st>>>(n, v, out);
-  chfsi_check_launch("vec_norm");
-}
 
-void vec_scale_inv(cudaStream_t st, int n, const double2* w, const double* nrm, double2* v) {
-  vec_scale_inv_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, w, nrm, v);
-  chfsi_check_launch("vec_scale_inv");
-}
 
-void lanczos_alpha(cudaStream_t st, int j, const double2* h1, const double2* h2,
-                   double* alpha) {
-  lanczos_alpha_kernel<<<1, 1, 0, st>>>(j, h1, h2, alpha);
-  chfsi_check_launch("lanczos_alpha");
-}
 
-void tridiag_bounds(cudaStream_t st, int m, const double* alpha, const double* beta,
-                    double* out4) {
-  tridiag_bounds_kernel<<<1, 32, 0, st>>>(m, alpha, beta, out4);
-  chfsi_check_launch("tridiag_bounds");
-}
 
 void residual_block(cudaStream_t st, int n, int k, const double2* HY, const double2* Y,
                     const double* lam, const int* perm, double2* R, double* lam_out) {
