@@ -5,7 +5,14 @@
 // The m steps run in ONE persistent cooperative kernel.  CTA g owns the
 // index range [g*chunk, (g+1)*chunk) twice over: as columns of H for the
 // mat-vec (w = H x = H^H x, so column c gives entry c; coalesced reads of
-// H, streamed past L1/L2) and as rows for every vector operation.  The
+// H, streamed past L1/L2) and as rows for every vector operation.
+//
+// The mat-vec does 4 real FMAs per 16 bytes of H: on GB300's narrow FP64
+// pipe that is ALU-bound at about a third of HBM speed.  It therefore reads
+// H as FP32 hi/lo pairs (split once per call, same 16 bytes per entry) and
+// runs on the FP32 pipe: exact hi*hi products (TwoProd), double-float sums,
+// hi*lo cross terms by FMA (about 2^-44 relative per partial sum); the
+// partial sums and everything after them are FP64.  The
 // mat-vec therefore hands each CTA exactly the rows it owns and needs no
 // grid barrier; a step has three: after the partial dots of each of the
 // two Gram-Schmidt passes and after the partial norms.  Partial sums are
@@ -41,9 +48,10 @@ struct LzArgs {
   int n, m;
   int chunk;     // indices owned per CTA
   int seg, nseg; // mat-vec column segments (rows per segment, count)
-  const double2* H;
+  const float4* Hs;  // H split into FP32 pairs: (re_hi, re_lo, im_hi, im_lo)
   double2* V;     // n x (m + 1), column-major
   double2* xbuf;  // 2 x n: the finished w of the previous step (ping-pong)
+  float4* xs;     // 2 x n: the same vectors split into FP32 pairs
   double2* p1;    // gridDim.x x (m + 1) partial dots, first pass
   double2* p2;    // same, second pass
   double* pn;     // gridDim.x partial squared norms
@@ -73,6 +81,57 @@ __device__ __forceinline__ void cmac_conj(double2& acc, double2 a, double2 b) {
   acc.x = fma(a.y, b.y, acc.x);
   acc.y = fma(a.x, b.y, acc.y);
   acc.y = fma(-a.y, b.x, acc.y);
+}
+
+__device__ __forceinline__ float4 split_c(double2 v) {
+  const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+  return make_float4(rh, __double2float_rn(v.x - (double)rh), ih,
+                     __double2float_rn(v.y - (double)ih));
+}
+
+// Double-float accumulator (hi, lo) for one real sum.
+struct DF {
+  float hi, lo;
+};
+// hi + p exactly as (hi', err) (Knuth's TwoSum); err goes to lo.
+// (Explicitly rounded intrinsics: no FMA contraction may touch these.)
+__device__ __forceinline__ void df_add(DF& s, float p) {
+  const float t = __fadd_rn(s.hi, p);
+  const float bp = __fsub_rn(t, s.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, bp)), __fsub_rn(p, bp)));
+  s.hi = t;
+}
+// s += a * b with the product exact (TwoProd by FMA)
+__device__ __forceinline__ void df_mac(DF& s, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  s.lo = __fadd_rn(s.lo, fmaf(a, b, -p));
+  df_add(s, p);
+}
+
+// acc += conj(h) x for h, x given as FP32 pairs.  The hi*hi products are
+// exact (TwoProd) and summed as double-float; the hi*lo cross terms are
+// below 2^-24 of them and go into the low word by plain FMAs; lo*lo
+// (2^-48) is dropped.  Relative accuracy about 2^-44 per partial sum.
+__device__ __forceinline__ void cmac_conj_split(DF& re, DF& im, float4 h, float4 x) {
+  // Re: hr xr + hi xi      Im: hr xi - hi xr
+  df_mac(re, h.x, x.x);
+  df_mac(re, h.z, x.z);
+  re.lo = fmaf(h.x, x.y, re.lo);
+  re.lo = fmaf(h.y, x.x, re.lo);
+  re.lo = fmaf(h.z, x.w, re.lo);
+  re.lo = fmaf(h.w, x.z, re.lo);
+  df_mac(im, h.x, x.z);
+  df_mac(im, -h.z, x.x);
+  im.lo = fmaf(h.x, x.w, im.lo);
+  im.lo = fmaf(h.y, x.z, im.lo);
+  im.lo = fmaf(-h.z, x.y, im.lo);
+  im.lo = fmaf(-h.w, x.x, im.lo);
+}
+
+__global__ void split_h_kernel(size_t count, const double2* __restrict__ H, float4* __restrict__ Hs) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x)
+    Hs[i] = split_c(__ldcs(H + i));
 }
 
 // Sum of the per-CTA partials P[g * ld + i], g = 0..G-1, by one warp in a
@@ -109,6 +168,7 @@ lanczos_persistent_kernel(LzArgs a) {
   for (int t = threadIdx.x; t < nown; t += LZ_THREADS) {
     const double2 s = start_entry(a.seed, r0 + t);
     a.xbuf[r0 + t] = s;
+    a.xs[r0 + t] = split_c(s);
     wl[t] = s;
     sq += s.x * s.x + s.y * s.y;
   }
@@ -139,29 +199,26 @@ lanczos_persistent_kernel(LzArgs a) {
 
   for (int j = 0; j < m; ++j) {
     // ---- w = H x / beta_prev on the owned columns (x = finished w) ------
-    const double2* x = a.xbuf + (size_t)(j & 1) * n;
+    const float4* x = a.xs + (size_t)(j & 1) * n;
     const double inv_b = 1.0 / bscal[0];
     const int ntask = nown * a.nseg;
     for (int t = warp; t < ntask; t += LZ_WARPS) {
       const int cl = t / a.nseg, s = t - cl * a.nseg;
-      const double2* col = a.H + (size_t)(r0 + cl) * n;
+      const float4* col = a.Hs + (size_t)(r0 + cl) * n;
       const int rs = s * a.seg, re = min(n, rs + a.seg);
-      // eight 16-byte loads of H in flight per lane
-      double2 acc[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) acc[u] = make_double2(0.0, 0.0);
+      // eight 16-byte loads of H in flight per lane, two accumulator pairs
+      DF ar[2] = {{0.f, 0.f}, {0.f, 0.f}}, ai[2] = {{0.f, 0.f}, {0.f, 0.f}};
       int r = rs + lane;
       for (; r + 224 < re; r += 256) {
-        double2 hv[8];
+        float4 hv[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) hv[u] = __ldcs(col + r + 32 * u);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) cmac_conj(acc[u & 3], hv[u], __ldcg(x + r + 32 * u));
+        for (int u = 0; u < 8; ++u) cmac_conj_split(ar[u & 1], ai[u & 1], hv[u], __ldcg(x + r + 32 * u));
       }
-      for (; r < re; r += 32) cmac_conj(acc[0], __ldcs(col + r), __ldcg(x + r));
-      double2 acc0 = acc[0];
-      acc0.x += acc[1].x + acc[2].x + acc[3].x;
-      acc0.y += acc[1].y + acc[2].y + acc[3].y;
+      for (; r < re; r += 32) cmac_conj_split(ar[0], ai[0], __ldcs(col + r), __ldcg(x + r));
+      double2 acc0 = make_double2(((double)ar[0].hi + (double)ar[0].lo) + ((double)ar[1].hi + (double)ar[1].lo),
+                                  ((double)ai[0].hi + (double)ai[0].lo) + ((double)ai[1].hi + (double)ai[1].lo));
       acc0 = warp_sum2(acc0);
       if (lane == 0) segp[t] = acc0;
     }
@@ -214,6 +271,7 @@ lanczos_persistent_kernel(LzArgs a) {
     for (int t = threadIdx.x; t < nown; t += LZ_THREADS) {
       const double2 w = wl[t];
       xn[r0 + t] = w;
+      a.xs[(size_t)((j + 1) & 1) * n + r0 + t] = split_c(w);
       sq += w.x * w.x + w.y * w.y;
     }
     sq = warp_sum(sq);
@@ -341,9 +399,13 @@ void lanczos_dev(chfsi_ctx* ctx, const double2* H, int n, int steps, unsigned lo
   a.chunk = chunk;
   a.seg = seg;
   a.nseg = nseg;
-  a.H = H;
+  float4* Hs = (float4*)ws_get(ctx, "lz_Hs", sizeof(float4) * (size_t)n * n);
+  split_h_kernel<<<ctx->sm_count * 8, 256, 0, st>>>((size_t)n * n, H, Hs);
+  chfsi_check_launch("split_h");
+  a.Hs = Hs;
   a.V = (double2*)ws_get(ctx, "lz_V", sizeof(double2) * (size_t)n * (m + 1));
   a.xbuf = (double2*)ws_get(ctx, "lz_x", sizeof(double2) * 2 * (size_t)n);
+  a.xs = (float4*)ws_get(ctx, "lz_xs", sizeof(float4) * 2 * (size_t)n);
   a.p1 = (double2*)ws_get(ctx, "lz_p1", sizeof(double2) * (size_t)G * (m + 1));
   a.p2 = (double2*)ws_get(ctx, "lz_p2", sizeof(double2) * (size_t)G * (m + 1));
   a.pn = (double*)ws_get(ctx, "lz_pn", sizeof(double) * (size_t)G);
