@@ -266,8 +266,13 @@ int chfsi_zgemm(chfsi_ctx* ctx, int op_a, int m, int n, int k, double alpha, con
  * place) against the nl orthonormal columns of L (complex n x nl; may be
  * NULL when nl = 0) by two block Gram-Schmidt passes and CholQR2 (shifted
  * CholQR3 when the Gram matrix is not numerically positive definite).
- * The result is the unique Q with R's diagonal real positive.  EBREAKDOWN if
- * the block is rank-deficient. */
+ * With the FP64 engine (opts.f64_gemm = CHFSI_GEMM_FP64) the result is the
+ * unique Q with R's diagonal real positive.  With CHFSI_GEMM_OZAKI the first
+ * Cholesky pass runs in FP32 arithmetic and, when it leaves
+ * ||I - Y^H Y||_F <= 0.1, the second is the polar correction
+ * Y (I - F)^{-1/2}, F = I - Y^H Y (binomial series): the result is then an
+ * orthonormal basis of the same span, not the Cholesky one (FP64 CholQR2
+ * otherwise).  EBREAKDOWN if the block is rank-deficient. */
 int chfsi_orthonormalize(chfsi_ctx* ctx, int n, int nl, const double* L, int k,
                          double* Y);
 

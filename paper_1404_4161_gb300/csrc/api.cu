@@ -242,9 +242,44 @@ void gemm_nn(chfsi_ctx* ctx, int M, int N, int K, const double2* A, int lda, con
 }
 
 // ------------------------------------------------- orthonormalisation ----
+// Y <- Y (I - F)^{-1/2} for the Hermitian F = I - Y^H Y with ||F||_F = f <
+// 1: the binomial series sum_m c_m F^m, c_0 = 1, c_m = c_{m-1} (2m-1)/(2m),
+// summed by Horner's rule to the first M with f^{M+1} / (1 - f) <= 2^-53,
+// so Y^H Y = I to rounding.  This is the symmetric (polar) orthonormal
+// basis of span(Y); its first-order term is the Newton-Schulz step
+// (3I - Y^H Y)/2.
+void polar_orthonormalize(chfsi_ctx* ctx, int n, int k, double2* Y, const double2* F, double f) {
+  cudaStream_t st = ctx->stream;
+  int M = 0;
+  while (M < 60 && std::pow(f, M + 1) / (1.0 - f) > 0x1p-53) ++M;
+  if (M == 0) return;
+  std::vector<double> c(M + 1);
+  c[0] = 1.0;
+  for (int m = 1; m <= M; ++m) c[m] = c[m - 1] * (2.0 * m - 1.0) / (2.0 * m);
+  double2* W = (double2*)ws_get(ctx, "pol_W", sizeof(double2) * (size_t)k * k);
+  double2* Tk = (double2*)ws_get(ctx, "pol_T", sizeof(double2) * (size_t)k * k);
+  shift_identity(st, k, nullptr, c[M], W);
+  for (int m = M - 1; m >= 0; --m) {
+    gemm_nn(ctx, k, k, k, F, k, W, k, Tk, k);  // F W
+    shift_identity(st, k, Tk, c[m], W);        // c_m I + F W
+  }
+  double2* T = (double2*)ws_get(ctx, "qr_T", sizeof(double2) * (size_t)n * k);
+  gemm_nn(ctx, n, k, k, Y, n, W, k, T, n);
+  CHFSI_CUDA_TRY(cudaMemcpyAsync(Y, T, sizeof(double2) * (size_t)n * k, cudaMemcpyDeviceToDevice,
+                                 st));
+}
+
 // The QR step of Alg. 1 on the device: two block Gram-Schmidt passes against the
 // locked block, column normalisation, then CholQR2 (a shifted Cholesky QR
 // pass first when the Gram matrix is not numerically positive definite).
+//
+// adaptive (the solver with the tensor-core FP64 products): the first
+// Cholesky pass runs in FP32 arithmetic -- it only has to precondition the
+// block -- and the second is replaced by the polar correction above when
+// ||I - Y^H Y||_F <= 0.1 after it.  The result is then an orthonormal
+// basis of the same span (not the Cholesky one), which is all that
+// Rayleigh-Ritz needs.  When the FP32 factorisation breaks down or leaves
+// the block further from orthonormal, the FP64 CholQR2 below takes over.
 void orthonormalize_dev(chfsi_ctx* ctx, int n, int nl, const double2* L, int k, double2* Y,
                         bool adaptive = false) {
   cudaStream_t st = ctx->stream;
@@ -261,6 +296,23 @@ void orthonormalize_dev(chfsi_ctx* ctx, int n, int nl, const double2* L, int k, 
   scale_columns_inv(st, n, k, Y, n, cn);
   double2* G = (double2*)ws_get(ctx, "qr_G", sizeof(double2) * (size_t)k * k);
   double2* T = (double2*)ws_get(ctx, "qr_T", sizeof(double2) * (size_t)n * k);
+  if (adaptive) {
+    gemm_cn(ctx, k, k, n, Y, n, Y, n, G, k);
+    hermitianize(st, k, G, k);
+    if (cholinv_upper_f32(ctx, k, G) == 0) {
+      gemm_nn(ctx, n, k, k, Y, n, G, k, T, n);
+      CHFSI_CUDA_TRY(cudaMemcpyAsync(Y, T, sizeof(double2) * (size_t)n * k,
+                                     cudaMemcpyDeviceToDevice, st));
+      gemm_cn(ctx, k, k, n, Y, n, Y, n, G, k);
+      hermitianize(st, k, G, k);
+      double2* F = (double2*)ws_get(ctx, "qr_F", sizeof(double2) * (size_t)k * k);
+      const double f = identity_defect(ctx, k, G, F);
+      if (f <= 0.1) {
+        polar_orthonormalize(ctx, n, k, Y, F, f);
+        return;
+      }
+    }
+  }
   double* shift = (double*)ws_get(ctx, "qr_shift", sizeof(double));
   int passes = 2;
   bool shifted = false;
@@ -1145,7 +1197,7 @@ int chfsi_orthonormalize(chfsi_ctx* ctx, int n, int nl, const double* L, int k, 
   return run_guarded(ctx, [&] {
     CHFSI_REQUIRE(n >= 1 && nl >= 0 && k >= 0 && nl + k <= n, "bad QR sizes");
     CHFSI_REQUIRE(Y && (nl == 0 || L), "bad QR buffers");
-    orthonormalize_dev(ctx, n, nl, C2(L), k, C2(Y));
+    orthonormalize_dev(ctx, n, nl, C2(L), k, C2(Y), use_oz(ctx));
   });
 }
 

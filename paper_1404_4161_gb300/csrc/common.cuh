@@ -156,6 +156,10 @@ int any_nonfinite(chfsi_ctx* ctx, size_t count, const double* v);
 // max |G - I| (synchronises) and T = (3I - G)/2 for a Newton-Schulz step.
 double deviation_from_identity(chfsi_ctx* ctx, int k, const double2* G);
 void ns_matrix(cudaStream_t st, int k, const double2* G, double2* T);
+// F = I - G (k x k) and ||F||_F (synchronises).
+double identity_defect(chfsi_ctx* ctx, int k, const double2* G, double2* F);
+// W = c I + T (T may be null: W = c I); W may alias T.
+void shift_identity(cudaStream_t st, int k, const double2* T, double c, double2* W);
 
 // Lanczos bounds of the spectrum (lanczos.cu): out4_dev = {theta_max +
 // beta_m, theta_min, theta_max, max|theta|}; NaN when a bounded wait of the
@@ -168,6 +172,8 @@ const int* lanczos_error_word(chfsi_ctx* ctx);
 // ld k; cholinv.cu).  Returns 0 or the order of the first leading minor
 // that is not positive definite (W then incomplete); synchronises.
 int cholinv_upper(chfsi_ctx* ctx, int k, double2* G);
+// The same with FP32 arithmetic (FP64 storage): a preconditioning pass.
+int cholinv_upper_f32(chfsi_ctx* ctx, int k, double2* G);
 
 // Loop control: locking, interval update, degrees, sorting (small_ops.cu).
 struct LoopCtl {

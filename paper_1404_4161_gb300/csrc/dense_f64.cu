@@ -456,7 +456,70 @@ __global__ void ns_matrix_kernel(int k, const double2* __restrict__ G, double2* 
     T[t] = make_double2(0.5 * ((i == j ? 3.0 : 0.0) - g.x), -0.5 * g.y);
   }
 }
+// F = I - G and per-block partial sums of |F_ij|^2
+__global__ void __launch_bounds__(256) identity_defect_kernel(int k, const double2* __restrict__ G,
+                                                              double2* __restrict__ F,
+                                                              double* __restrict__ part) {
+  __shared__ double sh[8];
+  double s = 0.0;
+  const size_t total = (size_t)k * k;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % k), j = (int)(t / k);
+    const double2 g = G[t];
+    const double2 f = make_double2((i == j ? 1.0 : 0.0) - g.x, -g.y);
+    F[t] = f;
+    s += f.x * f.x + f.y * f.y;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < 8; ++w) r += sh[w];
+    part[blockIdx.x] = r;
+  }
+}
+__global__ void sum_sqrt_kernel(int n, const double* part, double* out) {
+  if (threadIdx.x != 0) return;
+  double r = 0.0;
+  for (int i = 0; i < n; ++i) r += part[i];
+  *out = sqrt(r);
+}
+// W = c I + (T or 0)
+__global__ void shift_identity_kernel(int k, const double2* __restrict__ T, double c,
+                                      double2* __restrict__ W) {
+  const size_t total = (size_t)k * k;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(t % k), j = (int)(t / k);
+    double2 v = T ? T[t] : make_double2(0.0, 0.0);
+    if (i == j) v.x += c;
+    W[t] = v;
+  }
+}
 }  // namespace
+
+double identity_defect(chfsi_ctx* ctx, int k, const double2* G, double2* F) {
+  const unsigned nb = (unsigned)std::min<size_t>(((size_t)k * k + 255) / 256, 512);
+  double* part = (double*)ws_get(ctx, "idf_part", sizeof(double) * (nb + 2));
+  identity_defect_kernel<<<nb, 256, 0, ctx->stream>>>(k, G, F, part);
+  chfsi_check_launch("identity_defect");
+  sum_sqrt_kernel<<<1, 32, 0, ctx->stream>>>((int)nb, part, part + nb);
+  chfsi_check_launch("sum_sqrt");
+  double* h = (double*)pinned_get(ctx, 64);
+  CHFSI_CUDA_TRY(cudaMemcpyAsync(h, part + nb, sizeof(double), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+  CHFSI_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return *h;
+}
+
+void shift_identity(cudaStream_t st, int k, const double2* T, double c, double2* W) {
+  shift_identity_kernel<<<(unsigned)std::min<size_t>(((size_t)k * k + 255) / 256, 1024), 256, 0,
+                          st>>>(k, T, c, W);
+  chfsi_check_launch("shift_identity");
+}
 
 double deviation_from_identity(chfsi_ctx* ctx, int k, const double2* G) {
   const unsigned nb = (unsigned)std::min<size_t>(((size_t)k * k + 255) / 256, 512);

@@ -105,6 +105,34 @@ def test_update_shape_alpha_beta(ctx):
     assert rel < 1e-12
 
 
+@pytest.mark.parametrize("n,k,nl,cond", [(2000, 320, 0, 1.0), (1500, 333, 17, 1.0),
+                                         (3000, 100, 40, 1e5), (400, 24, 0, 1e11)])
+def test_orthonormalize_fp32_first_pass_polar(n, k, nl, cond):
+    """With the tensor-core FP64 engine the QR step runs its first Cholesky
+    pass in FP32 and a polar correction (binomial series) after it, falling
+    back to FP64 CholQR2 / shifted CholQR3 when the FP32 pass breaks down
+    (cond 1e11).  The result spans what Householder QR spans (to u * cond,
+    the accuracy to which that span is defined) and is orthonormal and
+    orthogonal to the locked block to FP64 rounding."""
+    Lk = oracle.orthonormalize(random_block(n, nl, 81)) if nl else None
+    base = random_block(n, k, 82)
+    Y = base @ np.diag(np.logspace(0, -np.log10(cond), k)) @ random_block(k, k, 83)
+    ref = oracle.orthonormalize(Y, Lk)
+    s = Chfsi(f64_gemm=L.GEMM_OZAKI)
+    Yc = to_dev_cm(Y)
+    s.orthonormalize(Yc, to_dev_cm(Lk) if nl else None)
+    s.close()
+    got = from_dev_cm(Yc)
+    assert np.abs(got.conj().T @ got - np.eye(k)).max() < 1e-13
+    if nl:
+        # the projection leaves L^H Y at the products' accuracy (~1e-15
+        # relative per entry); the two passes multiply it by ||W|| ~
+        # 1 / sigma_min(Y) (about 2 here) and mix k columns: ~sqrt(k) * 1e-14
+        assert np.abs(Lk.conj().T @ got).max() < 1e-14 * np.sqrt(k) * 3
+    span_diff = np.linalg.norm(got @ (got.conj().T @ ref) - ref)
+    assert span_diff < max(1e-12, 1e3 * 1.1e-16 * cond) * np.sqrt(k)
+
+
 def test_dfma_engine_same_entry(ctx):
     n, k = 300, 40
     H, lam, _ = known_problem(n, 9)
