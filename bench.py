@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--degrees", choices=["learned", "analytic"], default="learned")
+    ap.add_argument("--deg-warm", type=int, default=None,
+                    help="filter degree of the first loop on a warm start (library default 8)")
     ap.add_argument("--warm-rr", action="store_true",
                     help="Rayleigh-Ritz on each warm start before the first filter")
     ap.add_argument("--f64-gemm", choices=["ozaki", "fp64"], default="ozaki",
@@ -276,7 +278,8 @@ def main():
     prec = {"tc": L.PREC_TC, "mixed": L.PREC_MIXED, "fp64": L.PREC_FP64}[args.precision]
     f64g = L.GEMM_OZAKI if (args.f64_gemm == "ozaki" and prec != L.PREC_FP64) else L.GEMM_FP64
     warm_rr = 1 if (prec == L.PREC_TC and args.warm_rr) else 0
-    s = Chfsi(precision=prec, profile=1, f64_gemm=f64g, warm_rr=warm_rr)
+    extra = {"deg_warm": args.deg_warm} if args.deg_warm else {}
+    s = Chfsi(precision=prec, profile=1, f64_gemm=f64g, warm_rr=warm_rr, **extra)
     stream = torch.cuda.current_stream()
     train_info = None
     if args.degrees == "learned":

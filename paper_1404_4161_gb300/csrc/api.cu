@@ -284,13 +284,19 @@ void orthonormalize_dev(chfsi_ctx* ctx, int n, int nl, const double2* L, int k, 
                         bool adaptive = false) {
   cudaStream_t st = ctx->stream;
   if (k <= 0) return;
-  if (nl > 0) {
+  // Y -= L (L^H Y).  Whatever is left along L (rounding, ~u ||Y||) is
+  // multiplied by ||R^-1|| ~ 1/sigma_min(Y) in the first Cholesky pass, so
+  // one more projection follows that pass (the block is well conditioned
+  // by then and the second pass keeps what it leaves).
+  auto project = [&](int passes) {
+    if (nl <= 0) return;
     double2* P = (double2*)ws_get(ctx, "qr_P", sizeof(double2) * (size_t)nl * k);
-    for (int pass = 0; pass < 2; ++pass) {
+    for (int pass = 0; pass < passes; ++pass) {
       gemm_cn(ctx, nl, k, n, L, n, Y, n, P, nl);
       gemm_nn(ctx, n, k, nl, L, n, P, nl, Y, n, -1.0, 1.0);
     }
-  }
+  };
+  project(2);
   double* cn = (double*)ws_get(ctx, "qr_cn", sizeof(double) * k);
   column_norms(st, n, k, Y, n, cn);
   scale_columns_inv(st, n, k, Y, n, cn);
@@ -303,6 +309,7 @@ void orthonormalize_dev(chfsi_ctx* ctx, int n, int nl, const double2* L, int k, 
       gemm_nn(ctx, n, k, k, Y, n, G, k, T, n);
       CHFSI_CUDA_TRY(cudaMemcpyAsync(Y, T, sizeof(double2) * (size_t)n * k,
                                      cudaMemcpyDeviceToDevice, st));
+      project(1);
       gemm_cn(ctx, k, k, n, Y, n, Y, n, G, k);
       hermitianize(st, k, G, k);
       double2* F = (double2*)ws_get(ctx, "qr_F", sizeof(double2) * (size_t)k * k);
@@ -337,6 +344,7 @@ void orthonormalize_dev(chfsi_ctx* ctx, int n, int nl, const double2* L, int k, 
     gemm_nn(ctx, n, k, k, Y, n, G, k, T, n);
     CHFSI_CUDA_TRY(cudaMemcpyAsync(Y, T, sizeof(double2) * (size_t)n * k,
                                    cudaMemcpyDeviceToDevice, st));
+    if (pass < passes - 1) project(1);
     if (adaptive && pass == passes - 2) {
       // Before the last pass: when the block is already orthonormal to
       // 1e-8, one Newton-Schulz step Y (3I - Y^H Y)/2 leaves it orthonormal

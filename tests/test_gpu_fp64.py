@@ -99,6 +99,23 @@ def test_orthonormalize_parity(ctx, n, k, nl):
     assert np.abs(got.conj().T @ got - np.eye(k)).max() < 1e-13
 
 
+def test_orthonormalize_ill_conditioned_against_locked(ctx):
+    """An ill-conditioned block next to a locked one: what the projection
+    leaves along L is amplified by 1/sigma_min in the first Cholesky pass
+    and removed by the projection after it, so L^H Q stays at rounding."""
+    n, k, nl, cond = 3000, 100, 40, 1e6
+    Lk = oracle.orthonormalize(random_block(n, nl, 91))
+    Y = random_block(n, k, 92) @ np.diag(np.logspace(0, -np.log10(cond), k)) @ random_block(k, k, 93)
+    ref = oracle.orthonormalize(Y, Lk)
+    Yc = to_dev_cm(Y)
+    ctx.orthonormalize(Yc, to_dev_cm(Lk))
+    got = from_dev_cm(Yc)
+    assert np.abs(got.conj().T @ got - np.eye(k)).max() < 1e-13
+    assert np.abs(Lk.conj().T @ got).max() < 1e-14 * np.sqrt(k) * 3
+    span_diff = np.linalg.norm(got @ (got.conj().T @ ref) - ref)
+    assert span_diff < 1e3 * 1.1e-16 * cond * np.sqrt(k)
+
+
 @pytest.mark.parametrize("cond,k", [(1e9, 24), (1e11, 24), (1e11, 100)])
 def test_orthonormalize_ill_conditioned(ctx, cond, k):
     """Columns almost dependent (Gram matrix not numerically positive
