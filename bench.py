@@ -351,6 +351,7 @@ def main():
         pass
     k64_ms = sum(x["k_f64_ms"] for x in last)
     k64_fl = sum(x["k_f64_flops"] for x in last)
+    k64_fx = sum(x["k_f64_exec_flops"] for x in last)
     k64_n = sum(x["k_f64_launches"] for x in last)
     ktc_ms = sum(x["k_tc_ms"] for x in last)
     ktc_fl = sum(x["k_tc_flops"] for x in last)
@@ -361,13 +362,14 @@ def main():
     if k64_ms > 0:
         a = k64_fl / (k64_ms / 1e3) / 1e12
         oz = f64g == L.GEMM_OZAKI
+        ax = k64_fx / (k64_ms / 1e3) / 1e12  # executed: S(S+1)/2 BF16 slice products
         f64_roof = {"bound": "tensor" if oz else "alu",
-                    "achieved": 21.0 * a if oz else a,
+                    "achieved": ax if oz else a,
                     "peak": bf16_peak if oz else FP64_PEAK, "unit": "TFLOP/s",
-                    "frac": (21.0 * a / bf16_peak) if oz else a / FP64_PEAK, "traffic": None,
+                    "frac": (ax / bf16_peak) if oz else a / FP64_PEAK, "traffic": None,
                     "fp64_equivalent_tflops": a,
-                    "kernel": ("oz_gemm_kernel (FP64-accurate complex GEMM, 21 BF16 slice "
-                               "products per product)") if oz else
+                    "kernel": ("oz_gemm_kernel (FP64-accurate complex GEMM, S(S+1)/2 BF16 "
+                               "slice products per product: 28 at S = 7, 36 at S = 8)") if oz else
                               "zgemm_nn_kernel + zgemm_cn_part_kernel (FP64 complex GEMMs)",
                     "launches": int(k64_n), "avg_launch_ms": k64_ms / max(k64_n, 1),
                     "peak_source": ("bf16_tflops_sustained of measured" if oz else

@@ -117,11 +117,16 @@ typedef struct chfsi_stats {
   double k_tc_ms;           /* tcgen05 filter-step kernel                */
   double k_tc_flops;        /* its useful complex flops, 8 n^2 k_active  */
   long long k_tc_launches;
-  double k_solver_ms;       /* cuSOLVER k x k Cholesky / inverse / eigh  */
+  double k_solver_ms;       /* k x k factorisations: inverse Cholesky    */
+                            /* kernel and cuSOLVER's reduced eigensolve  */
   long long k_solver_calls;
   int loops_mlp;            /* loops whose degrees came from the MLP     */
   int mlp_fallback;         /* 1 if the MLP stalled and the analytic rule */
                             /* took over for the rest of this problem     */
+  double k_f64_exec_flops;  /* flops the FP64 GEMM kernels executed: with */
+                            /* the tensor-core engine S(S+1)/2 BF16 slice */
+                            /* products per product (S slices), else     */
+                            /* k_f64_flops                                */
 } chfsi_stats;
 
 /* ---- context ---------------------------------------------------------- */

@@ -41,7 +41,8 @@ class Stats(C.Structure):
                 ("k_f64_launches", C.c_longlong), ("k_tc_ms", C.c_double),
                 ("k_tc_flops", C.c_double), ("k_tc_launches", C.c_longlong),
                 ("k_solver_ms", C.c_double), ("k_solver_calls", C.c_longlong),
-                ("loops_mlp", C.c_int), ("mlp_fallback", C.c_int)]
+                ("loops_mlp", C.c_int), ("mlp_fallback", C.c_int),
+                ("k_f64_exec_flops", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

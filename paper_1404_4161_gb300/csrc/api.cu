@@ -37,18 +37,20 @@ int kt_begin(cudaStream_t st) {
     }
     t->cat.resize(t->ev.size() / 2);
     t->flops.resize(t->ev.size() / 2);
+    t->flops_exec.resize(t->ev.size() / 2);
   }
   const int slot = t->used++;
   CHFSI_CUDA_TRY(cudaEventRecord(t->ev[2 * slot], st));
   return slot;
 }
 
-void kt_end(cudaStream_t st, int slot, int cat, double flops) {
+void kt_end(cudaStream_t st, int slot, int cat, double flops, double flops_exec) {
   KernelTimer* t = g_kt;
   if (!t || slot < 0) return;
   CHFSI_CUDA_TRY(cudaEventRecord(t->ev[2 * slot + 1], st));
   t->cat[slot] = cat;
   t->flops[slot] = flops;
+  t->flops_exec[slot] = flops_exec < 0.0 ? flops : flops_exec;
 }
 
 void kt_resolve(KernelTimer* t) {
@@ -58,6 +60,7 @@ void kt_resolve(KernelTimer* t) {
     CHFSI_CUDA_TRY(cudaEventElapsedTime(&ms, t->ev[2 * i], t->ev[2 * i + 1]));
     t->ms[t->cat[i]] += ms;
     t->fl[t->cat[i]] += t->flops[i];
+    t->fx[t->cat[i]] += t->flops_exec[i];
     t->n[t->cat[i]] += 1;
   }
   t->used = 0;
@@ -720,6 +723,7 @@ void copy_kernel_times(chfsi_stats& S, const KernelTimer& t) {
   S.k_tc_launches = t.n[KT_TC];
   S.k_solver_ms = t.ms[KT_SOLVER];
   S.k_solver_calls = t.n[KT_SOLVER];
+  S.k_f64_exec_flops = t.fx[KT_F64];
 }
 
 struct TimerScope {

@@ -51,15 +51,19 @@ struct KernelTimer {
   std::vector<cudaEvent_t> ev;
   std::vector<int> cat;
   std::vector<double> flops;
+  std::vector<double> flops_exec;
   int used = 0;
   double ms[KT_NCAT] = {0, 0, 0};
   double fl[KT_NCAT] = {0, 0, 0};
+  double fx[KT_NCAT] = {0, 0, 0};  // executed flops (tensor-core slice products)
   long long n[KT_NCAT] = {0, 0, 0};
 };
 KernelTimer* kt_current();
 void kt_install(KernelTimer* t);
 int kt_begin(cudaStream_t st);                       // -1 when no timer
-void kt_end(cudaStream_t st, int slot, int cat, double flops);
+// flops: the operation's own count (FP64-equivalent for the Ozaki GEMM);
+// flops_exec: what the hardware executed (default: flops).
+void kt_end(cudaStream_t st, int slot, int cat, double flops, double flops_exec = -1.0);
 void kt_resolve(KernelTimer* t);
 
 // Kernel launches issued by this library (all contexts, all threads).

@@ -8,24 +8,26 @@
 // to [-1, 1] and cut into S slices of 7-bit signed digits (S = 7 for the
 // n-sized products, 8 for the k x k ones of the reduced eigensolve)
 //     x / scale = sum_{p=1..S} d_p 2^{-7p},  |d_1| <= 128, |d_p| <= 64,
-// which BF16 represents exactly.  Digit products are exact (<= 2^14) and
-// the sum of the pairs with p + q = t over a K chunk of 512 stays within
-// 2^24 (t = 2: 512 * 2^14; t = 7: 512 * 8 * 2^12), so the FP32 tensor-core
-// accumulation of each group t = 2..7 (one TMEM accumulator each) is
-// exact; the groups t >= 8 carry weights below 2^-35 of the leading one, so
-// their FP32 rounding stays below 2^-59.  Pairs with p + q > S + 1 are
-// dropped: with the slicing remainder (< 2^-7S) they bound the error by
-// ~2^-(7S-1) |scale_row| |scale_col| per product.
+// which BF16 represents exactly.  Digit products are exact (<= 2^14).  The
+// sum of the pairs with p + q = t over a K chunk of 512 is at most
+// 512 * 2^14 = 2^23 for t = 2 and 512 (2 * 2^13 + (t - 3) 2^12) =
+// 2^21 (t + 1) for t >= 3, within 2^24 for t <= 7: the FP32 tensor-core
+// accumulation of those groups (one TMEM accumulator each) is exact, and
+// the groups t = 8, 9 carry weights 2^-7t <= 2^-56 of the leading one, so
+// their FP32 rounding stays below 2^-78 of it.  Pairs with p + q > S + 1 are dropped: with
+// the slicing remainder (< 2^-7S) they bound the error by ~2^-(7S-1)
+// |scale_row| |scale_col| per product.  S(S+1)/2 slice products (28 for
+// S = 7, 36 for S = 8) per output tile and K step.
 //
 // The complex product is the real GEMM of the filter kernels:
 // C (M x 2N) = A (M x 2K) * B (2K x 2N), A rows [Re S | Im S] of the left
 // factor, B columns interleaved (Re T_j ; -Im T_j), (Im T_j ; Re T_j).
 //
 // Kernel layout (one 128 x 64 output tile per CTA, 384 threads):
-//   warp 0 lane 0: TMA producer (6 A slices + 6 B slices per 32-wide K block)
-//   warp 1 lane 0: tcgen05.mma issuer (21 slice pairs per 16-wide K step)
-//   warp 2:        TMEM allocation (6 groups x 64 columns)
-//   warps 4-11:    epilogue: after every 512-wide K chunk, drain the six
+//   warp 0 lane 0: TMA producer (S A slices + S B slices per 32-wide K block)
+//   warp 1 lane 0: tcgen05.mma issuer (S(S+1)/2 slice pairs per 16-wide K step)
+//   warp 2:        TMEM allocation (S groups x 64 columns)
+//   warps 4-11:    epilogue: after every 512-wide K chunk, drain the S
 //                  group accumulators into double-float running sums (two
 //                  warps per TMEM lane quarter, one per half of the
 //                  columns); at the end scale back and store FP64.
@@ -569,13 +571,26 @@ static void oz_run_t(chfsi_ctx* ctx, const OzOperand& A, const OzOperand& B, dou
   const int kblocks = (K2 + OZ_BK - 1) / OZ_BK;
   const int mt = (M + BM - 1) / BM, nt = (N2 + OZ_N - 1) / OZ_N;
   const int tiles = mt * nt;
-  // split K (in whole 512-chunks) when the tiles do not fill the GPU
-  int splits = 1;
+  // Split K in whole 512-chunks.  One CTA fits per SM, so the time is
+  // about (number of waves) x (K blocks per unit): pick the split that
+  // minimises that -- e.g. 320 tiles on 152 SMs take 3 waves unsplit (the
+  // last one 16 CTAs), 17 waves of 1/8 of K split 8 ways (2.1 in full-K
+  // units) -- plus a small charge per split for the FP64 partials that
+  // oz_reduce adds up.
   const int chunks = (kblocks + OZ_KC / OZ_BK - 1) / (OZ_KC / OZ_BK);
-  while (tiles * splits * 2 <= ctx->sm_count && splits * 2 <= chunks) splits *= 2;
-  const int chunks_per = (chunks + splits - 1) / splits;
-  const int kb_per = chunks_per * (OZ_KC / OZ_BK);
-  splits = (kblocks + kb_per - 1) / kb_per;
+  int kb_per = kblocks, splits = 1;
+  double best = 1e30;
+  for (int s = 1; s <= chunks; s *= 2) {
+    const int kp = ((chunks + s - 1) / s) * (OZ_KC / OZ_BK);
+    const int se = (kblocks + kp - 1) / kp;
+    const double waves = std::ceil((double)tiles * se / ctx->sm_count);
+    const double cost = waves * std::min(kp, kblocks) / kblocks + (se > 1 ? 0.03 * se : 0.0);
+    if (cost < best - 1e-9) {
+      best = cost;
+      kb_per = kp;
+      splits = se;
+    }
+  }
   const uint32_t stage_bytes = OZ_S * (BM * OZ_BK * 2 + OZ_N * OZ_BK * 2);
   int stages = (int)((220u * 1024u) / stage_bytes);
   stages = std::max(2, std::min(stages, 4));
@@ -617,7 +632,8 @@ static void oz_run_t(chfsi_ctx* ctx, const OzOperand& A, const OzOperand& B, dou
   const int slot = kt_begin(st);
   oz_gemm_kernel<OZ_S><<<grid, OZ_THREADS, smem, st>>>(mA, mB, p);
   chfsi_check_launch("oz_gemm");
-  kt_end(st, slot, KT_F64, 8.0 * (double)M * Nc * (K2 / 2));
+  kt_end(st, slot, KT_F64, 8.0 * (double)M * Nc * (K2 / 2),
+         (double)(OZ_S * (OZ_S + 1) / 2) * 2.0 * (double)M * N2 * K2);
   if (!direct) {
     const size_t total = (size_t)M * Nc;
     oz_reduce_kernel<<<(unsigned)std::min<size_t>((total + 255) / 256, 4096), 256, 0, st>>>(
