@@ -356,7 +356,7 @@ def main():
     ktc_ms = sum(x["k_tc_ms"] for x in last)
     ktc_fl = sum(x["k_tc_flops"] for x in last)
     ktc_n = sum(x["k_tc_launches"] for x in last)
-    FP64_PEAK = 1.10  # TFLOP/s, measured FP64 GEMM rate on this GB300 (profiles/peaks_probe_gb300.md)
+    FP64_PEAK = 1.10  # TFLOP/s, cuBLAS FP64 GEMM on this GB300 (python -m paper_1404_4161_gb300.peaks)
     bf16_peak = peaks.get("bf16_tflops_sustained", 1700.0)
     f64_roof = None
     if k64_ms > 0:
@@ -380,8 +380,8 @@ def main():
         a = 3.0 * ktc_fl / (ktc_ms / 1e3) / 1e12  # three BF16 products per complex product
         tc_roof = {"bound": "tensor", "achieved": a, "peak": bf16_peak, "unit": "TFLOP/s",
                    "frac": a / bf16_peak, "traffic": 179.7e6 if n == 4096 else None,
-                   "traffic_note": "dram read+write of one k_active=320 launch (ncu capture, "
-                                   "profiles/tc_filter_step_n4096_k320.md)",
+                   "traffic_note": "dram read+write of one k_active=320 launch (ncu --set full "
+                                   "capture of tc_filter_step_kernel at n = 4096)",
                    "useful_tflops": ktc_fl / (ktc_ms / 1e3) / 1e12,
                    "kernel": "tc_filter_step_kernel (BF16x3 tcgen05, fused recurrence)",
                    "launches": int(ktc_n), "avg_launch_ms": ktc_ms / max(ktc_n, 1),
