@@ -75,7 +75,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) 
 struct OzParams {
   int M, N2, K2;       // rows, real columns (2 x complex), real K (2 x complex)
   int kblocks;         // ceil(K2 / 32)
-  int kb_per_split;    // K blocks per split (multiple of 16 except the last)
+  int kb_per_split;    // K blocks per split
   int stages;
   const double* sA;    // row scales (powers of two), M
   const double* sB;    // column scales, N2
@@ -571,20 +571,23 @@ static void oz_run_t(chfsi_ctx* ctx, const OzOperand& A, const OzOperand& B, dou
   const int kblocks = (K2 + OZ_BK - 1) / OZ_BK;
   const int mt = (M + BM - 1) / BM, nt = (N2 + OZ_N - 1) / OZ_N;
   const int tiles = mt * nt;
-  // Split K in whole 512-chunks.  One CTA fits per SM, so the time is
-  // about (number of waves) x (K blocks per unit): pick the split that
+  // Split K.  One CTA fits per SM, so the time is about (number of waves)
+  // x (K blocks per unit + a fixed set-up and drain): pick the split that
   // minimises that -- e.g. 320 tiles on 152 SMs take 3 waves unsplit (the
-  // last one 16 CTAs), 17 waves of 1/8 of K split 8 ways (2.1 in full-K
-  // units) -- plus a small charge per split for the FP64 partials that
-  // oz_reduce adds up.
-  const int chunks = (kblocks + OZ_KC / OZ_BK - 1) / (OZ_KC / OZ_BK);
+  // last one 16 CTAs), 13 waves of 1/6 of K split 6 ways; the 30 tiles of
+  // a k x k product fill the GPU split 5 ways -- plus a small charge per
+  // split for the FP64 partials that oz_reduce adds up.  The exact-sum
+  // chunks (512 of K) are counted from each split's start, so any split
+  // stays exact.
   int kb_per = kblocks, splits = 1;
   double best = 1e30;
-  for (int s = 1; s <= chunks; s *= 2) {
-    const int kp = ((chunks + s - 1) / s) * (OZ_KC / OZ_BK);
+  for (int s = 1; s <= std::min(kblocks, 64); ++s) {
+    const int kp = (kblocks + s - 1) / s;
     const int se = (kblocks + kp - 1) / kp;
+    if (se != s) continue;
     const double waves = std::ceil((double)tiles * se / ctx->sm_count);
-    const double cost = waves * std::min(kp, kblocks) / kblocks + (se > 1 ? 0.03 * se : 0.0);
+    // a unit also pays a fixed set-up and drain of about 8 K blocks
+    const double cost = waves * (kp + 8.0) / (kblocks + 8.0) + (se > 1 ? 0.03 * se : 0.0);
     if (cost < best - 1e-9) {
       best = cost;
       kb_per = kp;
