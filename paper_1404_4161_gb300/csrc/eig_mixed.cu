@@ -200,6 +200,19 @@ void reduced_eigh_mixed(chfsi_ctx* ctx, int k, double2* G, double* w) {
     chfsi_check_launch("ns");
     oz_gemm_nn(ctx, k, k, k, W2, k, E, k, W, k, 1.0, 0.0, 8);
   }
+  // The refinement update can lose orthogonality at first order for pairs
+  // just outside the cluster threshold (E_ij ~ s_ij / gap), more than one
+  // Newton-Schulz step repairs; the Ritz vectors Q W must be orthonormal to
+  // rounding, or the locked block stops being one.  Newton-Schulz until
+  // max |W^H W - I| <= 1e-13 (quadratic: a few steps at most).
+  for (int extra = 0; extra < 6; ++extra) {
+    oz_gemm_cn(ctx, k, k, k, W, k, W, k, M, k, 1.0, 0.0, 8);
+    if (deviation_from_identity(ctx, k, M) <= 1e-13) break;  // synchronises
+    ns_kernel<<<grid_k2(k), 256, 0, st>>>(k, M, E);
+    chfsi_check_launch("ns");
+    CHFSI_CUDA_TRY(cudaMemcpyAsync(W2, W, sizeof(double2) * kk, cudaMemcpyDeviceToDevice, st));
+    oz_gemm_nn(ctx, k, k, k, W2, k, E, k, W, k, 1.0, 0.0, 8);
+  }
   double2* Wf = W;
   // Eigenvalues as the Rayleigh quotients of the final vectors: the lam of
   // a refinement step are quotients of that step's input and lag a step

@@ -187,3 +187,36 @@ def config_sequence(cfg: Config, seed: int, length: int | None = None,
     for _ in range(length - 1):
         hs.append(correlated_step(hs[-1], rng, eps, delta))
     return hs, lam
+
+
+def circulant_sequence(cfg: Config, seed: int, length: int = 2, eps: float | None = None,
+                       device=None):
+    """A cheap correlated sequence with an exactly known spectrum at the full
+    sizes, where a Haar eigenbasis would cost minutes of FP64 matmuls.
+
+    H_1 = D C D^H: C the Hermitian circulant whose eigenvalues are the
+    workload's spectrum lam (first column = FFT of lam / n; eigenvectors the
+    Fourier modes, dense and delocalised), D a diagonal of random phases.
+    H_{l+1} = E_l H_l E_l^H with E_l = diag(exp(i eps theta)), theta ~ N(0, 1):
+    same spectrum, eigenvectors turned by ~eps.  Returns (list of H as torch
+    complex128 tensors on ``device``, lam ascending)."""
+    import torch
+    eps = cfg.eps if eps is None else eps
+    n = cfg.n
+    rng = _rng(seed)
+    lam = two_band_spectrum(n, cfg.n_low, cfg.low, cfg.bulk, rng)
+    perm = rng.permutation(n)  # spread the wanted eigenvalues over the Fourier modes
+    col = np.fft.ifft(lam[perm])  # C[r, s] = col[(r - s) mod n]
+    phase = np.exp(2j * np.pi * rng.uniform(size=n))
+    col_t = torch.from_numpy(col).to(device)
+    idx = (torch.arange(n, device=device).unsqueeze(1) - torch.arange(n, device=device).unsqueeze(0)) % n
+    h = col_t[idx]
+    del idx
+    d = torch.from_numpy(phase).to(device)
+    h = d.unsqueeze(1) * h * d.conj().unsqueeze(0)
+    h = 0.5 * (h + h.conj().T)
+    hs = [h]
+    for _ in range(length - 1):
+        e = torch.from_numpy(np.exp(1j * eps * rng.standard_normal(n))).to(device)
+        hs.append(e.unsqueeze(1) * hs[-1] * e.conj().unsqueeze(0))
+    return hs, lam
