@@ -243,13 +243,19 @@ void residual_block(cudaStream_t st, int n, int k, const double2* HY, const doub
 void oz_hemm(chfsi_ctx* ctx, const std::string& prefix, const double2* H, int n,
              const double2* Q, int k, double2* Z, bool reslice_h);
 // ns = slices per operand: 6 (~2^-41 of the row x column scales), 7
-// (~2^-48) or 8 (~2^-55)
+// (~2^-48) or 8 (~2^-55); 0 = by size (oz_slices_for).
 void oz_gemm_cn(chfsi_ctx* ctx, int k1, int k2, int n, const double2* L, int ldl,
                 const double2* R, int ldr, double2* C, int ldc, double alpha, double beta,
-                int ns = 7);
+                int ns = 0);
 void oz_gemm_nn(chfsi_ctx* ctx, int m, int k2, int k1, const double2* S, int lds,
                 const double2* W, int ldw, double2* C, int ldc, double alpha, double beta,
-                int ns = 7);
+                int ns = 0);
+// Slices for a product whose largest dimension is `dim`: 7 up to 6144, 8
+// above.  The products' error grows with the reduction length (the
+// n-sized Gram and H Q products): with 7 slices the residuals of an
+// n = 8192 warm solve stall near 1e-10 (12 loops instead of 4) and an
+// n = 13000 solve does not reach it; 8 slices cost ~30% more tensor work.
+int oz_slices_for(int dim);
 int oz_check_error(chfsi_ctx* ctx);
 // Reduced Hermitian eigensolve: FP32 eigenpairs refined to FP64 accuracy
 // (eig_mixed.cu); eigenvectors overwrite G, eigenvalues ascending in w.

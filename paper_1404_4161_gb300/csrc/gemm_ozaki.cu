@@ -6,7 +6,8 @@
 // error-free splitting (Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59,
 // 2012): every operand row (A) and column (B) is scaled by a power of two
 // to [-1, 1] and cut into S slices of 7-bit signed digits (S = 7 for the
-// n-sized products, 8 for the k x k ones of the reduced eigensolve)
+// n-sized products up to n = 6144 and 8 above, 8 for the k x k ones of the
+// reduced eigensolve)
 //     x / scale = sum_{p=1..S} d_p 2^{-7p},  |d_1| <= 128, |d_p| <= 64,
 // which BF16 represents exactly.  Digit products are exact (<= 2^14).  The
 // sum of the pairs with p + q = t over a K chunk of 512 is at most
@@ -43,7 +44,7 @@ using namespace tcx;
 namespace {
 
 constexpr int OZ_S_MAX = 8;    // slices per operand: 6, 7 or 8
-constexpr int OZ_S_LARGE = 7;  // the n-sized products of QR and Rayleigh-Ritz
+constexpr int OZ_SIZE_SWITCH = 6144;  // above: 8 slices for the n-sized products
 constexpr int OZ_BETA = 7;     // bits per slice
 constexpr int OZ_BK = 32;      // K block (64-byte swizzle rows)
 constexpr int OZ_N = 64;       // tile columns (real)
@@ -695,18 +696,21 @@ static void oz_slice_bb(cudaStream_t st, int rows, int ldt, const double2* T, in
 // a dense Hermitian matrix is often far larger than its other entries and
 // would otherwise set each row's scale.  The sliced H - mu I is kept in the
 // workspace named after `prefix` and rebuilt when reslice_h is set.
+int oz_slices_for(int dim) { return dim > OZ_SIZE_SWITCH ? 8 : 7; }
+
 void oz_hemm(chfsi_ctx* ctx, const std::string& prefix, const double2* H, int n,
              const double2* Q, int k, double2* Z, bool reslice_h) {
   OzOperand A, B;
-  oz_alloc(ctx, prefix + "ozH", A, n, 2 * n, OZ_S_LARGE);
+  const int ns = oz_slices_for(n);
+  oz_alloc(ctx, prefix + "ozH", A, n, 2 * n, ns);
   double* mu = (double*)ws_get(ctx, (prefix + "ozH.mu").c_str(), sizeof(double));
   if (reslice_h) {
     oz_diag_mean_kernel<<<1, 256, 0, ctx->stream>>>(n, H, mu);
     chfsi_check_launch("oz_diag_mean");
-    oz_slice_a_conj<OZ_S_LARGE>(ctx->stream, n, n, H, n, A, mu);
+    OZ_DISPATCH(ns, oz_slice_a_conj, ctx->stream, n, n, H, n, A, mu);
   }
-  oz_alloc(ctx, "ozQ", B, 2 * k, 2 * n, OZ_S_LARGE);
-  oz_slice_bb<OZ_S_LARGE>(ctx->stream, n, n, Q, k, B);
+  oz_alloc(ctx, "ozQ", B, 2 * k, 2 * n, ns);
+  OZ_DISPATCH(ns, oz_slice_bb, ctx->stream, n, n, Q, k, B);
   oz_run(ctx, A, B, Z, n, 1.0, 0.0);
   const size_t total = (size_t)n * k;
   oz_add_shift_kernel<<<(unsigned)std::min<size_t>((total + 255) / 256, 4096), 256, 0,
@@ -718,6 +722,7 @@ void oz_hemm(chfsi_ctx* ctx, const std::string& prefix, const double2* H, int n,
 void oz_gemm_cn(chfsi_ctx* ctx, int k1, int k2, int n, const double2* L, int ldl,
                 const double2* R, int ldr, double2* C, int ldc, double alpha, double beta,
                 int ns) {
+  if (ns <= 0) ns = oz_slices_for(std::max(n, std::max(k1, k2)));
   OzOperand A, B;
   oz_alloc(ctx, "ozL", A, k1, 2 * n, ns);
   OZ_DISPATCH(ns, oz_slice_a_conj, ctx->stream, n, ldl, L, k1, A, nullptr);
@@ -730,6 +735,7 @@ void oz_gemm_cn(chfsi_ctx* ctx, int k1, int k2, int n, const double2* L, int ldl
 void oz_gemm_nn(chfsi_ctx* ctx, int m, int k2, int k1, const double2* S, int lds,
                 const double2* W, int ldw, double2* C, int ldc, double alpha, double beta,
                 int ns) {
+  if (ns <= 0) ns = oz_slices_for(std::max(m, std::max(k1, k2)));
   OzOperand A, B;
   oz_alloc(ctx, "ozS", A, m, 2 * k1, ns);
   OZ_DISPATCH(ns, oz_slice_a_row, ctx->stream, k1, lds, S, m, A);
