@@ -43,7 +43,6 @@ using namespace tcx;
 
 namespace {
 
-constexpr int OZ_S_MAX = 8;    // slices per operand: 6, 7 or 8
 constexpr int OZ_SIZE_SWITCH = 6144;  // above: 8 slices for the n-sized products
 constexpr int OZ_BETA = 7;     // bits per slice
 constexpr int OZ_BK = 32;      // K block (64-byte swizzle rows)
