@@ -169,7 +169,8 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": f"correlated sequence of {length} complex128 Hermitian problems, "
                                f"n={n}, nev={nev}, nex={nex}, tol 1e-10",
-                   "l2": "inputs larger than L2"},
+                   "l2": ("inputs larger than L2" if 16 * n * n > 129e6 else
+                          "inputs smaller than L2 (reduced-size run)")},
         "cpu_baseline": {"kind": "oracle", "value": val, "unit": UNIT, "cores": cores,
                          "sample": sample},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -459,7 +460,9 @@ def main():
                        "precision": args.precision, "degree_model": args.degrees,
                        "f64_products": "ozaki (tensor cores)" if f64g == L.GEMM_OZAKI else "fp64 pipe",
                        "warm_rayleigh_ritz": bool(warm_rr),
-                       "l2": "inputs larger than L2 (each H is 16 n^2 bytes)",
+                       "l2": (f"inputs larger than L2 (each H is 16 n^2 = {16 * n * n / 1e6:.0f} MB)"
+                              if 16 * n * n > 129e6 else
+                              "inputs smaller than L2 (reduced-size run; not a bench value)"),
                        "parallelism": f"replicas x{ws}"},
             "filter_tflops": filter_tflops,
             "filter_tflops_lowp_share": lowp_flops / filt_flops if filt_flops else 0.0,
