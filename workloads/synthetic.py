@@ -218,5 +218,6 @@ def circulant_sequence(cfg: Config, seed: int, length: int = 2, eps: float | Non
     hs = [h]
     for _ in range(length - 1):
         e = torch.from_numpy(np.exp(1j * eps * rng.standard_normal(n))).to(device)
-        hs.append(e.unsqueeze(1) * hs[-1] * e.conj().unsqueeze(0))
+        h = e.unsqueeze(1) * hs[-1] * e.conj().unsqueeze(0)
+        hs.append(0.5 * (h + h.conj().T))
     return hs, lam
