@@ -228,10 +228,12 @@ void gemm_cn(chfsi_ctx* ctx, int K1, int K2, int Nr, const double2* A, int lda,
 }
 
 // C = alpha A B + beta C (C may be the same buffer as the beta term only)
+// (oz_ns: slices of the tensor-core engine, 0 = by the product's size)
 void gemm_nn(chfsi_ctx* ctx, int M, int N, int K, const double2* A, int lda, const double2* B,
-             int ldb, double2* C, int ldc, double alpha = 1.0, double beta = 0.0) {
+             int ldb, double2* C, int ldc, double alpha = 1.0, double beta = 0.0,
+             int oz_ns = 0) {
   if (use_oz(ctx)) {
-    oz_gemm_nn(ctx, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta);
+    oz_gemm_nn(ctx, M, N, K, A, lda, B, ldb, C, ldc, alpha, beta, oz_ns);
     return;
   }
   EpiNN ep;
@@ -262,9 +264,11 @@ void polar_orthonormalize(chfsi_ctx* ctx, int n, int k, double2* Y, const double
   double2* W = (double2*)ws_get(ctx, "pol_W", sizeof(double2) * (size_t)k * k);
   double2* Tk = (double2*)ws_get(ctx, "pol_T", sizeof(double2) * (size_t)k * k);
   shift_identity(st, k, nullptr, c[M], W);
+  // the k x k products take the slice count of the problem's n-sized ones
+  const int ns = oz_slices_for(n);
   for (int m = M - 1; m >= 0; --m) {
-    gemm_nn(ctx, k, k, k, F, k, W, k, Tk, k);  // F W
-    shift_identity(st, k, Tk, c[m], W);        // c_m I + F W
+    gemm_nn(ctx, k, k, k, F, k, W, k, Tk, k, 1.0, 0.0, ns);  // F W
+    shift_identity(st, k, Tk, c[m], W);                      // c_m I + F W
   }
   double2* T = (double2*)ws_get(ctx, "qr_T", sizeof(double2) * (size_t)n * k);
   gemm_nn(ctx, n, k, k, Y, n, W, k, T, n);
