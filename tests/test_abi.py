@@ -46,3 +46,13 @@ def test_library_loads_and_binding_matches(libpath):
     o = _lib.default_opts()
     assert (o.deg_max, o.deg_extra, o.lanczos_steps) == (36, 1, 20)
     assert _lib.lib().chfsi_strerror(_lib.ENOCONV) == b"not converged within max_loops"
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: with the library missing, the binding raises instead
+    of computing anything."""
+    from paper_1404_4161_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB", str(tmp_path / "libchfsi_missing.so"))
+    with pytest.raises(ImportError):
+        _lib.lib()
