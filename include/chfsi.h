@@ -22,6 +22,10 @@
  *    exits the process or traps on the device.  chfsi_strerror() names a
  *    code; chfsi_last_error() gives a message for the last failure on ctx.
  *  - Not thread-safe per context: one host thread per chfsi_ctx at a time.
+ *  - Diagnostics: with the environment variable CHFSI_VERBOSE=1 the solvers
+ *    print one line per outer loop on stderr (loop, active and locked
+ *    columns, residual range of the wanted pairs, filter interval, summed
+ *    degrees).  This adds a device-to-host copy per loop.
  */
 #ifndef CHFSI_H
 #define CHFSI_H

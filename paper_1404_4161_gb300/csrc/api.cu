@@ -10,6 +10,8 @@
 // to size the next launches.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <vector>
@@ -659,6 +661,7 @@ struct Problem {
       S.mlp_fallback = 1;
     }
     max_resid_wanted = ctl_h->max_resid_wanted;
+    if (verbose()) log_loop(n_new, ctl_h);
     if (nl >= nev) {
       status = CHFSI_OK;
       done = true;
@@ -689,6 +692,33 @@ struct Problem {
       degs.assign(deg_h, deg_h + ka);
       if (loops >= o->max_loops) done = true;
     }
+  }
+
+  // CHFSI_VERBOSE=1: one line per loop on stderr (diagnostics only).
+  static bool verbose() {
+    static const bool v = [] {
+      const char* e = std::getenv("CHFSI_VERBOSE");
+      return e && e[0] == '1';
+    }();
+    return v;
+  }
+  void log_loop(int n_new, const LoopCtl* c) {
+    std::vector<double> r(ka + n_new);
+    CHFSI_CUDA_TRY(cudaMemcpy(r.data(), res, sizeof(double) * r.size(), cudaMemcpyDeviceToHost));
+    std::vector<double> l(ka + n_new);
+    CHFSI_CUDA_TRY(cudaMemcpy(l.data(), lam, sizeof(double) * l.size(), cudaMemcpyDeviceToHost));
+    const int nw = std::min((int)r.size(), nev - (nl - n_new));
+    std::vector<double> w(r.begin(), r.begin() + std::max(nw, 0));
+    std::sort(w.begin(), w.end());
+    int worst = 0;
+    for (int j = 1; j < nw; ++j)
+      if (r[j] > r[worst]) worst = j;
+    std::fprintf(stderr,
+                 "[chfsi] step %d loop %d n %d k_act %d locked %d (+%d) wanted resid: min %.2e "
+                 "med %.2e max %.2e (col %d, ritz %.6f) alpha %.4f gamma %.4f sum_deg %lld\n",
+                 step, loops, n, (int)r.size(), nl, n_new, w.empty() ? 0.0 : w.front(),
+                 w.empty() ? 0.0 : w[w.size() / 2], w.empty() ? 0.0 : w.back(), worst,
+                 nw > 0 ? l[worst] : 0.0, c->alpha, c->gamma, sdeg);
   }
 
   // Output: locked pairs ascending, then the remaining active block.

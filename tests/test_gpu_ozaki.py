@@ -178,9 +178,11 @@ def test_solve_with_tensor_core_fp64_products():
 
 @pytest.mark.parametrize("n,k", [(700, 48), (2048, 320)])
 def test_rayleigh_ritz_mixed_eigensolver(ctx, n, k):
-    """With the tensor-core engine the k x k eigensolve is FP32 + two
-    Ogita-Aishima refinement steps + Newton-Schulz: Ritz values to 1e-12
-    ||H||, Ritz vectors orthonormal to 1e-13 k, residual block consistent."""
+    """With the tensor-core engine the k x k eigensolve is a refinement on
+    FP64-accurate products (here from the identity: Q is close to
+    eigenvectors, so the Rayleigh quotient is nearly diagonal): Ritz values
+    to 1e-12 ||H||, Ritz vectors orthonormal to 1e-13 k, residual block
+    consistent."""
     H, lam, q = known_problem(n, 80 + n)
     Q = oracle.orthonormalize(q[:, :k] + 1e-3 * random_block(n, k, 81 + n))
     s = Chfsi(f64_gemm=L.GEMM_OZAKI)
