@@ -32,6 +32,10 @@ sys.path.insert(0, ROOT)
 METRIC = "filter TFLOP/s and s per eigenproblem at resid≤1e-10: mixed+learned vs FP64"
 UNIT = "s/eigenproblem"
 SEQ_SEED_OFFSET = 2000
+# DRAM bytes (read + write) of one tc_filter_step_kernel launch, from an ncu
+# capture of the kernel as it stands, per n (None: not captured).
+TC_FILTER_TRAFFIC: dict = {}
+TC_FILTER_TRAFFIC_NOTE = "no capture of the current filter kernel yet"
 
 
 def parse():
@@ -43,8 +47,14 @@ def parse():
     ap.add_argument("--precision", choices=["tc", "mixed", "fp64"], default="tc")
     ap.add_argument("--n", type=int, default=None, help="override n (smaller test runs)")
     ap.add_argument("--length", type=int, default=None)
-    ap.add_argument("--fp64-compare", type=int, default=2,
-                    help="also time the plain FP64 path on this many problems")
+    ap.add_argument("--fp64-compare", type=int, default=-1,
+                    help="also time the plain FP64 GPU path on this many problems of the same "
+                         "sequence (-1: all of them, 0: skip)")
+    ap.add_argument("--cpu-budget", type=float, default=90.0,
+                    help="seconds of oracle work on the host cores: the CPU baseline solves "
+                         "the sequence's problems in order until this is spent")
+    ap.add_argument("--no-certify", action="store_true",
+                    help="skip the untimed per-problem residual and eigenvalue checks")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--degrees", choices=["learned", "analytic"], default="learned")
@@ -52,6 +62,10 @@ def parse():
                     help="filter degree of the first loop on a warm start (library default 8)")
     ap.add_argument("--warm-rr", action="store_true",
                     help="Rayleigh-Ritz on each warm start before the first filter")
+    ap.add_argument("--warm-resid", type=int, choices=[0, 1], default=0,
+                    help="warm starts: residuals of the starting block on the new H, per-vector "
+                         "first-loop degrees (1) or the uniform deg_warm (0, the library default); "
+                         "the FP64 comparison always uses 1, its faster setting")
     ap.add_argument("--f64-gemm", choices=["ozaki", "fp64"], default="ozaki",
                     help="engine of the FP64 products in the tc/mixed modes")
     ap.add_argument("--batched-scale", type=float, default=0.25,
@@ -178,20 +192,27 @@ def run_reference(args):
     }))
 
 
-def cpu_baseline_sample(Hs_host, nev, nex, tol, X0, length):
-    """Oracle on the host cores, bounded: problem 1 (random start) and
-    problem 2 (warm start) of the sequence, extrapolated like the
-    reference arm."""
+def cpu_baseline_sample(Hs_host, nev, nex, tol, X0, budget_s):
+    """Oracle on the host cores over the same sequence: problems in order
+    (problem 1 from the random block, each later one warm from its
+    predecessor's Ritz vectors), until the budget is spent; the value is the
+    mean over the problems solved."""
     import oracle
-    t0 = time.perf_counter()
-    r1 = oracle.chfsi(Hs_host[0], nev, nex, X0, tol)
-    t1 = time.perf_counter()
-    oracle.chfsi(Hs_host[1], nev, nex, r1["X"], tol, warm=(r1["evals"][0], r1["evals"][-1]))
-    t2 = time.perf_counter()
-    val = ((t1 - t0) + (length - 1) * (t2 - t1)) / length
-    return {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"problems 1 (random start) and 2 (warm start), value = (t1 + "
-                      f"{length - 1} t2)/{length}; t1 {t1 - t0:.2f} s, t2 {t2 - t1:.2f} s"}
+    times, X, warm = [], X0, None
+    t_start = time.perf_counter()
+    for l, H in enumerate(Hs_host):
+        t0 = time.perf_counter()
+        r = oracle.chfsi(H, nev, nex, X, tol, warm=warm)
+        times.append(time.perf_counter() - t0)
+        X, warm = r["X"], (r["evals"][0], r["evals"][-1])
+        if time.perf_counter() - t_start > budget_s:
+            break
+    done = len(times)
+    return {"value": float(np.mean(times)), "unit": UNIT, "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": (f"problems 1..{done} of the {len(Hs_host)}-problem sequence "
+                       f"(problem 1 from the random block), value = their mean; per problem "
+                       + ", ".join(f"{t:.2f}" for t in times) + " s")}
 
 
 def measure_batched(scale, dev, stream, prec):
@@ -280,7 +301,8 @@ def main():
     f64g = L.GEMM_OZAKI if (args.f64_gemm == "ozaki" and prec != L.PREC_FP64) else L.GEMM_FP64
     warm_rr = 1 if (prec == L.PREC_TC and args.warm_rr) else 0
     extra = {"deg_warm": args.deg_warm} if args.deg_warm else {}
-    s = Chfsi(precision=prec, profile=1, f64_gemm=f64g, warm_rr=warm_rr, **extra)
+    s = Chfsi(precision=prec, profile=1, f64_gemm=f64g, warm_rr=warm_rr,
+              warm_resid=args.warm_resid, **extra)
     stream = torch.cuda.current_stream()
     train_info = None
     if args.degrees == "learned":
@@ -307,8 +329,14 @@ def main():
         ev, sts, rc = s.solve_sequence(Hcs, nev, nex, Xc, cfg.tol)
         return ev, sts, rc, Xc
 
+    def require_ok(rc, sts, what):
+        bad = [l for l, x in enumerate(sts) if x["status"] != L.OK]
+        if rc != L.OK or bad:
+            raise RuntimeError(f"{what}: rc {rc}, problems not converged: {bad}")
+
     for _ in range(args.warmup):
-        step()
+        _, sts, rc, _ = step()
+        require_ok(rc, sts, "warm-up step")
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
@@ -316,27 +344,58 @@ def main():
     clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    stats_all = []
+    stats_all, rcs = [], []
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(args.steps):
         ev, sts, rc, Xc = step()
         stats_all.append(sts)
+        rcs.append(rc)
     e1.record(stream)
     torch.cuda.synchronize()
     ck = clocks.stop()
+    for rc, sts in zip(rcs, stats_all):
+        require_ok(rc, sts, "timed step")
     from paper_1404_4161_gb300 import dist as D
     # every rank solved its own replica of the sequence: all ranks' problems
     # over the slowest rank's time
     sec_per_problem, t_max, _ = D.whole_job_seconds_per_unit(
         length, e0.elapsed_time(e1) / args.steps / 1e3, dev)
     ms = 1e3 * t_max
+    ev_timed = ev.clone()
 
-    # correctness of the timed result (residual certificate, on the device)
-    Xl = Xc.t()[:, :nev]
-    Hl = Hcs[-1].t()
-    R = torch.linalg.vector_norm(Hl @ Xl - Xl * ev[-1, :nev].to(Xl.dtype), dim=0)
-    max_res = float(R.max()) / max(abs(float(lam[0])), abs(float(lam[-1])))
+    # Certificate of the timed result, untimed: the same sequence problem by
+    # problem through chfsi_solve (same arithmetic: warm start from the
+    # previous problem's lam_1, lam_k, step index set), and for every
+    # problem the residuals ||H x - lam x|| / ||H|| of the nev wanted pairs
+    # in FP64 (torch on the device); the eigenvalues of the first and the
+    # last problem against numpy's eigvalsh (LAPACK, host).
+    cert = None
+    if not args.no_certify:
+        normH = max(abs(float(lam[0])), abs(float(lam[-1])))
+        Xc = X0c.clone()
+        warm, resid, same, statuses = None, [], 0.0, []
+        for l in range(length):
+            s.set_opts(step0=l)
+            evl, stl, rcl = s.solve(Hcs[l], nev, nex, Xc, cfg.tol, warm=warm)
+            statuses.append(int(stl["status"]))
+            Xl = Xc.t()[:, :nev]
+            Hl = Hcs[l].t()
+            R = torch.linalg.vector_norm(Hl @ Xl - Xl * evl[:nev].to(Xl.dtype), dim=0)
+            resid.append(float(R.max()) / normH)
+            same = max(same, float((evl - ev_timed[l]).abs().max()))
+            warm = (float(evl[0]), float(evl[-1]))
+        s.set_opts(step0=0)
+        eig_err = {}
+        for l in sorted({0, length - 1}):
+            w = np.linalg.eigvalsh(Hcs[l].t().cpu().numpy())
+            eig_err[l] = float(np.abs(ev_timed[l, :nev].cpu().numpy() - w[:nev]).max() / normH)
+        cert = {"status_per_problem": statuses, "max_resid_per_problem": resid,
+                "max_resid_all": max(resid),
+                "eigvalsh_err_rel_normH": {str(k): v for k, v in eig_err.items()},
+                "max_abs_diff_vs_timed_evals": same}
+        if max(statuses) != L.OK or max(resid) > cfg.tol or max(eig_err.values()) > 1e-12:
+            raise RuntimeError(f"certificate failed: {cert}")
 
     last = stats_all[-1]
     filt_ms = sum(x["ms_filter"] for x in last)
@@ -350,15 +409,13 @@ def main():
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    k64_ms = sum(x["k_f64_ms"] for x in last)
-    k64_fl = sum(x["k_f64_flops"] for x in last)
-    k64_fx = sum(x["k_f64_exec_flops"] for x in last)
-    k64_n = sum(x["k_f64_launches"] for x in last)
-    ktc_ms = sum(x["k_tc_ms"] for x in last)
-    ktc_fl = sum(x["k_tc_flops"] for x in last)
-    ktc_n = sum(x["k_tc_launches"] for x in last)
+    tot = lambda key: sum(x[key] for x in last)
+    k64_ms, k64_fl, k64_fx, k64_n = (tot("k_f64_ms"), tot("k_f64_flops"),
+                                     tot("k_f64_exec_flops"), tot("k_f64_launches"))
+    ktc_ms, ktc_fl, ktc_n = tot("k_tc_ms"), tot("k_tc_flops"), tot("k_tc_launches")
     FP64_PEAK = 1.10  # TFLOP/s, cuBLAS FP64 GEMM on this GB300 (python -m paper_1404_4161_gb300.peaks)
     bf16_peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
     f64_roof = None
     if k64_ms > 0:
         a = k64_fl / (k64_ms / 1e3) / 1e12
@@ -380,15 +437,35 @@ def main():
     if ktc_ms > 0:
         a = 3.0 * ktc_fl / (ktc_ms / 1e3) / 1e12  # three BF16 products per complex product
         tc_roof = {"bound": "tensor", "achieved": a, "peak": bf16_peak, "unit": "TFLOP/s",
-                   "frac": a / bf16_peak, "traffic": 179.7e6 if n == 4096 else None,
-                   "traffic_note": "dram read+write of one k_active=320 launch (ncu --set full "
-                                   "capture of tc_filter_step_kernel at n = 4096)",
+                   "frac": a / bf16_peak, "traffic": TC_FILTER_TRAFFIC.get(n),
+                   "traffic_note": TC_FILTER_TRAFFIC_NOTE,
                    "useful_tflops": ktc_fl / (ktc_ms / 1e3) / 1e12,
                    "kernel": "tc_filter_step_kernel (BF16x3 tcgen05, fused recurrence)",
                    "launches": int(ktc_n), "avg_launch_ms": ktc_ms / max(ktc_n, 1),
                    "peak_source": "bf16_tflops_sustained of measured"}
-    cands = [r for r in (f64_roof, tc_roof) if r is not None]
+    lz_ms = tot("k_lanczos_ms")
+    lz_roof = None
+    if lz_ms > 0:
+        # 20 Lanczos steps read the FP32 split of H (16 n^2 B) once each
+        lz_bytes = length * 20 * 16.0 * n * n
+        a = lz_bytes / (lz_ms / 1e3) / 1e9
+        lz_roof = {"bound": "hbm", "achieved": a, "peak": hbm_peak, "unit": "GB/s",
+                   "frac": a / hbm_peak, "traffic": None,
+                   "kernel": "lanczos_persistent_kernel (20 steps, FP32 hi/lo split of H)",
+                   "launches": length, "avg_launch_ms": lz_ms / length,
+                   "peak_source": "hbm_gbs of measured"}
+    # every timed kernel family, library or not; the roofline object is the
+    # family with the most device time among those with a roofline
+    kernel_ms = {"ozaki_gemm" if f64g == L.GEMM_OZAKI else "fp64_gemm": k64_ms,
+                 "tc_filter": ktc_ms, "cusolver_fp32_eig_start": tot("k_solver_ms"),
+                 "cholinv": tot("k_cholinv_ms"), "lanczos": lz_ms,
+                 "ozaki_slicers": tot("k_slice_ms"), "eig_control": tot("k_eigctl_ms")}
+    kernel_ms["other (phases minus the above)"] = max(0.0, sum(
+        x["ms_" + p] for x in last for p in ["lanczos", "filter", "qr", "rr", "resid", "lock"])
+        - sum(kernel_ms.values()))
+    cands = [r for r in (f64_roof, tc_roof, lz_roof) if r is not None]
     roof = max(cands, key=lambda r: r["avg_launch_ms"] * r["launches"]) if cands else None
+    dominant = max(kernel_ms, key=kernel_ms.get)
 
     # end to end: same solve through the C ABI with host buffers
     e2e = None
@@ -401,41 +478,54 @@ def main():
         t0 = time.perf_counter()
         for _ in range(reps):
             Xh.copy_(X0h)
-            s.solve_sequence_host(Hh, nev, nex, Xh, cfg.tol)
+            _, sts_h, rc_h = s.solve_sequence_host(Hh, nev, nex, Xh, cfg.tol)
+            require_ok(rc_h, sts_h, "end-to-end step")
         t1 = time.perf_counter()
         e2e = {"value": (t1 - t0) / reps / (length * ws), "unit": UNIT,
                "h2d_bytes_per_step": int(length * 16 * n * n + 16 * n * k),
                "d2h_bytes_per_step": int(16 * n * k + 8 * length * k)}
+        del Hh
+
+    def timed_sequence(solver):
+        Xc = X0c.clone()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, sts_x, rc_x = solver.solve_sequence(Hcs, nev, nex, Xc, cfg.tol)
+        b.record(stream)
+        torch.cuda.synchronize()
+        require_ok(rc_x, sts_x, "comparison run")
+        return a.elapsed_time(b) / 1e3, sts_x
 
     analytic_cmp = None
     if args.degrees == "learned":
         s.set_opts(degree_model=L.DEG_ANALYTIC)
-        Xc = X0c.clone()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        _, sts_a, _ = s.solve_sequence(Hcs, nev, nex, Xc, cfg.tol)
-        b.record(stream)
-        torch.cuda.synchronize()
-        analytic_cmp = {"s_per_problem": a.elapsed_time(b) / 1e3 / length,
-                        "loops": [x["loops"] for x in sts_a]}
+        t_a, sts_a = timed_sequence(s)
+        analytic_cmp = {"s_per_problem": t_a / length, "loops": [x["loops"] for x in sts_a],
+                        "col_degrees": [x["col_degrees"] for x in sts_a]}
         s.set_opts(degree_model=L.DEG_MLP)
 
     fp64_cmp = None
-    if args.fp64_compare and prec != L.PREC_FP64:
-        s64 = Chfsi(precision=L.PREC_FP64)
-        m = args.fp64_compare
-        Xc = X0c.clone()
-        s64.solve_sequence(Hcs[:m], nev, nex, Xc, cfg.tol)
+    m64 = length if args.fp64_compare < 0 else min(args.fp64_compare, length)
+    if m64 and prec != L.PREC_FP64:
+        s64 = Chfsi(precision=L.PREC_FP64, warm_resid=1)
+        Xw = X0c.clone()
+        s64.solve(Hcs[0], nev, nex, Xw, cfg.tol)  # warm-up (kernels, workspaces)
         torch.cuda.synchronize()
         Xc = X0c.clone()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        _, sts64, _ = s64.solve_sequence(Hcs[:m], nev, nex, Xc, cfg.tol)
+        _, sts64, rc64 = s64.solve_sequence(Hcs[:m64], nev, nex, Xc, cfg.tol)
         b.record(stream)
         torch.cuda.synchronize()
-        fp64_cmp = {"s_per_problem": a.elapsed_time(b) / 1e3 / m, "problems": m}
+        require_ok(rc64, sts64, "FP64 comparison")
+        fp64_cmp = {"s_per_problem": a.elapsed_time(b) / 1e3 / m64, "problems": m64,
+                    "loops": [x["loops"] for x in sts64],
+                    "same_sequence_as_headline": m64 == length,
+                    "config": "FP64 filter, FP64 products, analytic degrees, warm starts with "
+                              "residual-based first-loop degrees (opts.warm_resid = 1: one loop "
+                              "per warm problem instead of two)"}
         s64.close()
 
     batched = None
@@ -443,9 +533,9 @@ def main():
         batched = measure_batched(args.batched_scale, dev, stream, prec)
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline and length >= 2:
-        Hh2 = [Hcs[0].t().cpu().numpy(), Hcs[1].t().cpu().numpy()]
-        cpu = cpu_baseline_sample(Hh2, nev, nex, cfg.tol, X0, length)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        Hh_np = [h.t().cpu().numpy() for h in Hcs]
+        cpu = cpu_baseline_sample(Hh_np, nev, nex, cfg.tol, X0, args.cpu_budget)
 
     if rank == 0:
         out = {
@@ -460,21 +550,26 @@ def main():
                        "precision": args.precision, "degree_model": args.degrees,
                        "f64_products": "ozaki (tensor cores)" if f64g == L.GEMM_OZAKI else "fp64 pipe",
                        "warm_rayleigh_ritz": bool(warm_rr),
+                       "warm_residual_start": bool(args.warm_resid),
                        "l2": (f"inputs larger than L2 (each H is 16 n^2 = {16 * n * n / 1e6:.0f} MB)"
                               if 16 * n * n > 129e6 else
                               "inputs smaller than L2 (reduced-size run; not a bench value)"),
                        "parallelism": f"replicas x{ws}"},
+            "status_per_problem": [int(x["status"]) for x in last],
             "filter_tflops": filter_tflops,
             "filter_tflops_lowp_share": lowp_flops / filt_flops if filt_flops else 0.0,
-            "max_resid": max_res,
+            "max_resid": cert["max_resid_all"] if cert else None,
+            "certificate": cert,
             "loops": [x["loops"] for x in last],
+            "col_degrees": [x["col_degrees"] for x in last],
             "phase_ms": {p: sum(x["ms_" + p] for x in last)
                          for p in ["lanczos", "filter", "qr", "rr", "resid", "lock"]},
-            "kernel_ms": {"fp64_products": k64_ms, "tc_filter": ktc_ms,
-                          "cusolver_kxk": sum(x["k_solver_ms"] for x in last)},
+            "kernel_ms": kernel_ms,
+            "dominant_kernel_bucket": dominant,
             "roofline": roof,
             "filter_roofline": tc_roof,
             "fp64_gemm_roofline": f64_roof,
+            "lanczos_roofline": lz_roof,
             "gpu_launches": int(launches),
             "filter_launches_per_step": int(filt_launch),
             "clocks": ck,

@@ -96,6 +96,12 @@ typedef struct chfsi_opts {
                        /* block before the first filter, so the first loop */
                        /* gets per-vector degrees and (CHFSI_PREC_TC) the  */
                        /* refinement form (0: the paper's uniform deg)     */
+  int warm_resid;      /* 1: on a warm start, the Rayleigh quotients and  */
+                       /* residuals of the starting block on the new H    */
+                       /* (one product H X, no reduced eigensolve): pairs */
+                       /* already converged lock, the first loop gets     */
+                       /* per-vector degrees and (CHFSI_PREC_TC) the      */
+                       /* refinement form; 0: the uniform deg_warm (0)    */
 } chfsi_opts;
 
 /* Per-problem statistics (host struct, filled when non-NULL). */
@@ -121,8 +127,8 @@ typedef struct chfsi_stats {
   double k_tc_ms;           /* tcgen05 filter-step kernel                */
   double k_tc_flops;        /* its useful complex flops, 8 n^2 k_active  */
   long long k_tc_launches;
-  double k_solver_ms;       /* k x k factorisations: inverse Cholesky    */
-                            /* kernel and cuSOLVER's reduced eigensolve  */
+  double k_solver_ms;       /* cuSOLVER calls: the FP32 start of the      */
+                            /* reduced eigensolve on dense quotients      */
   long long k_solver_calls;
   int loops_mlp;            /* loops whose degrees came from the MLP     */
   int mlp_fallback;         /* 1 if the MLP stalled and the analytic rule */
@@ -131,6 +137,12 @@ typedef struct chfsi_stats {
                             /* the tensor-core engine S(S+1)/2 BF16 slice */
                             /* products per product (S slices), else     */
                             /* k_f64_flops                                */
+  /* more per-kernel device times (opts.profile = 1): */
+  double k_cholinv_ms;      /* inverse-Cholesky kernel of the QR step    */
+  double k_lanczos_ms;      /* Lanczos kernels of the spectral bounds    */
+  double k_slice_ms;        /* operand slicers of the tensor-core engine */
+  double k_eigctl_ms;       /* control kernels of the reduced eigensolve */
+                            /* (analysis, cluster rotations)             */
 } chfsi_stats;
 
 /* ---- context ---------------------------------------------------------- */

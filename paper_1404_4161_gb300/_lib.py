@@ -26,7 +26,7 @@ class Opts(C.Structure):
                 ("deg_max", C.c_int), ("deg_extra", C.c_int), ("lanczos_steps", C.c_int),
                 ("max_loops", C.c_int), ("switch_tol", C.c_double), ("seed", C.c_ulonglong),
                 ("profile", C.c_int), ("mlp_extra", C.c_int), ("step0", C.c_int),
-                ("f64_gemm", C.c_int), ("warm_rr", C.c_int)]
+                ("f64_gemm", C.c_int), ("warm_rr", C.c_int), ("warm_resid", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -42,7 +42,9 @@ class Stats(C.Structure):
                 ("k_tc_flops", C.c_double), ("k_tc_launches", C.c_longlong),
                 ("k_solver_ms", C.c_double), ("k_solver_calls", C.c_longlong),
                 ("loops_mlp", C.c_int), ("mlp_fallback", C.c_int),
-                ("k_f64_exec_flops", C.c_double)]
+                ("k_f64_exec_flops", C.c_double), ("k_cholinv_ms", C.c_double),
+                ("k_lanczos_ms", C.c_double), ("k_slice_ms", C.c_double),
+                ("k_eigctl_ms", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -126,6 +126,8 @@ void validate_opts(const chfsi_opts& o) {
   CHFSI_REQUIRE(o.max_loops >= 1, "opts.max_loops");
   CHFSI_REQUIRE(o.switch_tol > 0.0, "opts.switch_tol");
   CHFSI_REQUIRE(o.mlp_extra >= 0 && o.step0 >= 0, "opts.mlp_extra/step0");
+  CHFSI_REQUIRE((o.warm_rr == 0 || o.warm_rr == 1) && (o.warm_resid == 0 || o.warm_resid == 1),
+                "opts.warm_rr/warm_resid");
   CHFSI_REQUIRE(o.f64_gemm == CHFSI_GEMM_FP64 || o.f64_gemm == CHFSI_GEMM_OZAKI,
                 "opts.f64_gemm");
 }
@@ -426,7 +428,7 @@ struct Problem {
   LoopCtl* ctl = nullptr;
   double beta = 0, norm_h = 0, alpha = 0, gamma = 0, max_resid_wanted = INFINITY;
   int ka = 0, nl = 0, loops = 0, status = CHFSI_ENOCONV;
-  bool use_mlp = false, lowp_on = false, done = false;
+  bool use_mlp = false, lowp_on = false, done = false, warm_start = false;
   std::vector<int> degs;
   chfsi_stats S;
   long long launches0 = 0, fl0 = 0;
@@ -524,6 +526,7 @@ struct Problem {
     S.norm_h = norm_h;
     int deg0;
     if (warm) {
+      warm_start = true;
       gamma = warm[0];
       alpha = warm[1];
       deg0 = o->deg_warm;
@@ -551,6 +554,40 @@ struct Problem {
       mark(6);
       after_rr();
       S.ms_rr += ms(4, 5);
+    } else if (warm && o->warm_resid) {
+      // The warm block (the previous problem's Ritz vectors, orthonormal)
+      // on the new H: its Rayleigh quotients and residuals from one product
+      // H X, without a reduced eigensolve.  Converged pairs lock at once,
+      // the first loop gets per-vector degrees from the rule of Sec. 3.2,
+      // and with CHFSI_PREC_TC the refinement form of the filter, which
+      // holds for any diagonal of shifts.
+      mark(3);
+      mark(4);
+      hx_product(Xact, Yf);  // Yf <- H Xact (scratch)
+      rayleigh_quotients(st, n, ka, Yf, Xact, res);
+      sort_by_value(st, ka, res, perm);
+      gather_values(st, ka, res, perm, lam);
+      gather_columns(st, n, ka, Xact, n, perm, Yrr, n);
+      gather_columns(st, n, ka, Yf, n, perm, HY, n);
+      mark(5);
+      residual_norms(st, n, ka, HY, Yrr, lam, norm_h, res);
+      mark(6);
+      after_rr();
+      S.ms_rr += ms(4, 5);
+    }
+  }
+
+  // Z = H Y (n x ka) with the engine of the FP64 products; the tensor-core
+  // slices of H are made once per problem and shared with Rayleigh-Ritz.
+  void hx_product(const double2* Y, double2* Z) {
+    if (use_oz(ctx)) {
+      oz_hemm(ctx, pre, H, n, Y, ka, Z, !h_sliced);
+      h_sliced = true;
+    } else {
+      EpiNN ep;
+      ep.D = Z;
+      ep.ldd = n;
+      zgemm_nn(st, n, ka, n, H, n, Y, n, ep);
     }
   }
 
@@ -668,7 +705,11 @@ struct Problem {
       mark(7);
       CHFSI_CUDA_TRY(cudaStreamSynchronize(st));
     } else {
-      alpha = ctl_h->alpha;
+      // Courant-Fischer makes the largest Ritz value of the block an upper
+      // bound of lambda_k; on a warm start the interval keeps the tightest
+      // bound seen (the previous problem's lambda_k first), so that a buffer
+      // column the low-precision filter spoiled cannot push alpha up.
+      alpha = warm_start ? std::min(alpha, ctl_h->alpha) : ctl_h->alpha;
       const double c2 = c_(), e2 = e_();
       if (use_mlp) {
         mlp_degrees(ctx, ka, lam, res, act_idx, c2, e2, gamma, step, tol, deg);
@@ -758,6 +799,10 @@ void copy_kernel_times(chfsi_stats& S, const KernelTimer& t) {
   S.k_solver_ms = t.ms[KT_SOLVER];
   S.k_solver_calls = t.n[KT_SOLVER];
   S.k_f64_exec_flops = t.fx[KT_F64];
+  S.k_cholinv_ms = t.ms[KT_CHOLINV];
+  S.k_lanczos_ms = t.ms[KT_LANCZOS];
+  S.k_slice_ms = t.ms[KT_SLICE];
+  S.k_eigctl_ms = t.ms[KT_EIGCTL];
 }
 
 struct TimerScope {
@@ -891,6 +936,7 @@ void chfsi_default_opts(chfsi_opts* o) {
   o->step0 = 0;
   o->f64_gemm = CHFSI_GEMM_FP64;
   o->warm_rr = 0;
+  o->warm_resid = 0;
 }
 
 const char* chfsi_strerror(int code) {

@@ -347,7 +347,7 @@ int cholinv_run(chfsi_ctx* ctx, int k, double2* G) {
   CHFSI_CUDA_TRY(cudaLaunchCooperativeKernel((void*)cholinv_kernel<R>, dim3(grid),
                                              dim3(CI_THREADS), args, smem, st));
   chfsi_check_launch("cholinv");
-  kt_end(st, slot, KT_SOLVER, 0.0);
+  kt_end(st, slot, KT_CHOLINV, 0.0);
   int* h = (int*)pinned_get(ctx, 64);
   CHFSI_CUDA_TRY(cudaMemcpyAsync(h, a.flags, 3 * sizeof(int) + 8, cudaMemcpyDeviceToHost, st));
   CHFSI_CUDA_TRY(cudaStreamSynchronize(st));

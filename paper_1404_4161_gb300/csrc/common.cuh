@@ -42,21 +42,27 @@ struct ChfsiError {
     if (!(cond)) throw ChfsiError{CHFSI_EINVAL, text};                         \
   } while (0)
 
-// Optional per-launch timing of the two dominant kernel families.  When a
+// Optional per-launch timing of the kernel families.  When a
 // timer is installed for the calling thread (solver with opts.profile),
 // kt_begin / kt_end bracket a launch with CUDA events on its stream and
 // kt_resolve adds the elapsed times after the stream has been synchronised.
-enum KtCat { KT_F64 = 0, KT_TC = 1, KT_SOLVER = 2, KT_NCAT = 3 };
+// Categories: FP64 products (Ozaki or DFMA GEMMs), the tensor-core filter,
+// cuSOLVER calls, the inverse-Cholesky kernel, the Lanczos kernels, the
+// Ozaki operand slicers, and the control kernels of the reduced eigensolve.
+enum KtCat {
+  KT_F64 = 0, KT_TC = 1, KT_SOLVER = 2, KT_CHOLINV = 3, KT_LANCZOS = 4, KT_SLICE = 5,
+  KT_EIGCTL = 6, KT_NCAT = 7
+};
 struct KernelTimer {
   std::vector<cudaEvent_t> ev;
   std::vector<int> cat;
   std::vector<double> flops;
   std::vector<double> flops_exec;
   int used = 0;
-  double ms[KT_NCAT] = {0, 0, 0};
-  double fl[KT_NCAT] = {0, 0, 0};
-  double fx[KT_NCAT] = {0, 0, 0};  // executed flops (tensor-core slice products)
-  long long n[KT_NCAT] = {0, 0, 0};
+  double ms[KT_NCAT] = {};
+  double fl[KT_NCAT] = {};
+  double fx[KT_NCAT] = {};  // executed flops (tensor-core slice products)
+  long long n[KT_NCAT] = {};
 };
 KernelTimer* kt_current();
 void kt_install(KernelTimer* t);
@@ -149,6 +155,9 @@ void column_norms(cudaStream_t st, int n, int k, const double2* Y, int ldy, doub
 void scale_columns_inv(cudaStream_t st, int n, int k, double2* Y, int ldy, const double* norms);
 void residual_norms(cudaStream_t st, int n, int k, const double2* HY, const double2* Y,
                     const double* lam, double norm_h, double* out);
+// lam_j = Re(y_j^H hy_j) / (y_j^H y_j) for the k columns (ld n).
+void rayleigh_quotients(cudaStream_t st, int n, int k, const double2* HY, const double2* Y,
+                        double* lam);
 void gather_columns(cudaStream_t st, int n, int k, const double2* src, int lds,
                     const int* idx, double2* dst, int ldd);
 void gather_values(cudaStream_t st, int k, const double* src, const int* idx, double* dst);

@@ -224,6 +224,23 @@ residual_norms_kernel(int n, const double2* __restrict__ HY, const double2* __re
   if (threadIdx.x == 0) out[blockIdx.x] = sqrt(s) * inv_norm;
 }
 
+// lam_j = Re(y_j^H hy_j) / (y_j^H y_j): the Rayleigh quotient of column j.
+__global__ void __launch_bounds__(256)
+rayleigh_quotients_kernel(int n, const double2* __restrict__ HY, const double2* __restrict__ Y,
+                          double* lam) {
+  __shared__ double sh[8];
+  const size_t off = (size_t)blockIdx.x * n;
+  double num = 0.0, den = 0.0;
+  for (int r = threadIdx.x; r < n; r += 256) {
+    const double2 h = HY[off + r], y = Y[off + r];
+    num += y.x * h.x + y.y * h.y;
+    den += y.x * y.x + y.y * y.y;
+  }
+  num = block_sum<256>(num, sh);
+  den = block_sum<256>(den, sh);
+  if (threadIdx.x == 0) lam[blockIdx.x] = num / den;
+}
+
 __global__ void hermitianize_kernel(int k, double2* G, int ldg) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y;
@@ -367,6 +384,13 @@ void residual_norms(cudaStream_t st, int n, int k, const double2* HY, const doub
   if (k <= 0) return;
   residual_norms_kernel<<<k, 256, 0, st>>>(n, HY, Y, lam, 1.0 / norm_h, out);
   chfsi_check_launch("residual_norms");
+}
+
+void rayleigh_quotients(cudaStream_t st, int n, int k, const double2* HY, const double2* Y,
+                        double* lam) {
+  if (k <= 0) return;
+  rayleigh_quotients_kernel<<<k, 256, 0, st>>>(n, HY, Y, lam);
+  chfsi_check_launch("rayleigh_quotients");
 }
 
 void gather_columns(cudaStream_t st, int n, int k, const double2* src, int lds, const int* idx,

@@ -45,7 +45,9 @@ namespace {
 
 constexpr int EV_BAND = 16;        // hard pairs are searched this far apart in sorted order
 constexpr int EV_CHUNK = 32;       // largest block one warp diagonalises
-constexpr int EV_WARPS = 4;        // warps (clusters) per CTA of the cluster kernel
+constexpr int EV_WARPS = 4;        // warps (clusters) per CTA of the cluster kernels
+constexpr int EV_ROWS = 64;        // rows (columns) per CTA of the rotation updates
+constexpr int EV_SMALL = 8;        // larger clusters on the identity start: FP32 start instead
 constexpr int EV_LD = EV_CHUNK + 1;
 constexpr double EV_TAU = 1e-2;    // first-order update only where |update| <= tau
 constexpr double EV_ETA = 1e-12;   // converged off-diagonal, relative to max |lam|
@@ -155,30 +157,72 @@ ev_scan_kernel(int k, const double2* __restrict__ S, const double2* __restrict__
 }
 
 // Cluster list from reach[]: positions p and p + 1 belong to one cluster
-// when some hard pair (q, q + d) has q <= p < q + d.  Clusters are split
-// into blocks of at most EV_CHUNK consecutive positions: clist[b] = (first
-// position, size), blocks of size 1 dropped.  One thread (k is at most a
-// few thousand).
-__global__ void ev_clusters_kernel(int k, const int* __restrict__ reach, EvCtl* ctl,
-                                   int2* __restrict__ clist) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int nc = 0, mx = 0, start = -1, maxend = -1;
-  for (int p = 0; p < k; ++p) {
-    maxend = max(maxend, p + reach[p]);
-    const bool link = maxend > p;
-    if (link && start < 0) start = p;
-    if (!link && start >= 0) {
-      const int size = p - start + 1;
+// when some hard pair (q, q + d) has q <= p < q + d, i.e. when
+// max_{q <= p} (q + reach[q]) > p.  Clusters are split into blocks of at
+// most EV_CHUNK consecutive positions: clist[b] = (first position, size),
+// blocks of size 1 dropped.  One CTA of 1024 threads, each owning a
+// contiguous segment of positions: a block-wide max-scan gives the links,
+// a block-wide sum-scan the output slots.
+constexpr int EVC_T = 1024;
+__global__ void __launch_bounds__(EVC_T)
+ev_clusters_kernel(int k, const int* __restrict__ reach, unsigned char* __restrict__ link,
+                   EvCtl* ctl, int2* __restrict__ clist) {
+  __shared__ int sh[EVC_T];
+  const int t = threadIdx.x;
+  const int L = (k + EVC_T - 1) / EVC_T;
+  const int p0 = min(k, t * L), p1 = min(k, p0 + L);
+  // 1. links: exclusive max-scan of the segment maxima of (q + reach[q])
+  int m = -1;
+  for (int p = p0; p < p1; ++p) m = max(m, p + reach[p]);
+  sh[t] = m;
+  __syncthreads();
+  for (int o = 1; o < EVC_T; o <<= 1) {
+    const int v = t >= o ? sh[t - o] : -1;
+    __syncthreads();
+    sh[t] = max(sh[t], v);
+    __syncthreads();
+  }
+  int run = t > 0 ? sh[t - 1] : -1;
+  __syncthreads();
+  for (int p = p0; p < p1; ++p) {
+    run = max(run, p + reach[p]);
+    link[p] = run > p ? 1 : 0;
+  }
+  __syncthreads();
+  // 2. clusters start at p with link[p] and not link[p - 1]; the owner of
+  // a start walks to its end and counts its blocks
+  int nblk = 0, mx = 0;
+  for (int p = p0; p < p1; ++p) {
+    if (link[p] && (p == 0 || !link[p - 1])) {
+      int e = p;
+      while (link[e]) ++e;  // link[k - 1] is 0: the walk stops inside the array
+      const int size = e - p + 1;
       mx = max(mx, size);
-      for (int a = start; a <= p; a += EV_CHUNK) {
-        const int m = min(EV_CHUNK, p - a + 1);
-        if (m >= 2) clist[nc++] = make_int2(a, m);
-      }
-      start = -1;
+      nblk += size / EV_CHUNK + (size % EV_CHUNK >= 2 ? 1 : 0);
     }
   }
-  ctl->n_clusters = nc;
-  ctl->max_cluster = mx;
+  sh[t] = nblk;
+  __syncthreads();
+  for (int o = 1; o < EVC_T; o <<= 1) {
+    const int v = t >= o ? sh[t - o] : 0;
+    __syncthreads();
+    sh[t] += v;
+    __syncthreads();
+  }
+  int slot = sh[t] - nblk;
+  const int total = sh[EVC_T - 1];
+  for (int p = p0; p < p1; ++p) {
+    if (link[p] && (p == 0 || !link[p - 1])) {
+      int e = p;
+      while (link[e]) ++e;
+      for (int a = p; a <= e; a += EV_CHUNK) {
+        const int sz = min(EV_CHUNK, e - a + 1);
+        if (sz >= 2) clist[slot++] = make_int2(a, sz);
+      }
+    }
+  }
+  if (mx) atomicMax(&ctl->max_cluster, mx);
+  if (t == 0) ctl->n_clusters = total;
 }
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
@@ -191,30 +235,10 @@ __device__ __forceinline__ double2 cscale(double2 a, double s) {
   return make_double2(a.x * s, a.y * s);
 }
 
-// y[:, cidx[q]] <- sum_p y[:, cidx[p]] V[p][q] for the k rows of the
-// column-major k x k matrix Y (one warp; rows in groups of 32 staged through
-// the warp's buffer T, 32 x EV_LD; V[p][q] at V[q * EV_LD + p]).
-__device__ void apply_right(int k, double2* __restrict__ Y, const int* cidx, int m,
-                            const double2* V, double2* T, int lane) {
-  for (int r0 = 0; r0 < k; r0 += 32) {
-    const int r = r0 + lane;
-    __syncwarp();
-    if (r < k)
-      for (int p = 0; p < m; ++p) T[lane * EV_LD + p] = Y[(size_t)cidx[p] * k + r];
-    __syncwarp();
-    if (r < k)
-      for (int q = 0; q < m; ++q) {
-        double2 acc = make_double2(0.0, 0.0);
-        for (int p = 0; p < m; ++p) acc = cadd(acc, cmul(T[lane * EV_LD + p], V[q * EV_LD + p]));
-        Y[(size_t)cidx[q] * k + r] = acc;
-      }
-  }
-}
-
 // One warp per cluster block: cyclic Jacobi on the block A = S[c, c]
-// (positions a0 .. a0 + m - 1 in ascending lam, indices perm[]), V the
-// accumulated rotation; then W[:, c], S[:, c] and M[:, c] are multiplied by
-// V on the right and V is stored for the row update (ev_cluster_rows).
+// (positions a0 .. a0 + m - 1 in ascending lam, indices perm[]); the
+// accumulated rotation V (m x m, V[p][q] at Vstore[ci][q * EV_CHUNK + p])
+// is stored for the updates of W, S and M.
 // The rotation of pair (p, q), with a_pq = |a_pq| e^{i phi}, is the
 // unitary U = [[cs, sn e^{i phi}], [-sn e^{-i phi}, cs]] where (cs, sn)
 // is the real symmetric Schur rotation of [[a_pp, |a_pq|], [|a_pq|, a_qq]]
@@ -222,9 +246,8 @@ __device__ void apply_right(int k, double2* __restrict__ Y, const int* cidx, int
 // sqrt(1 + zeta^2)), cs = 1 / sqrt(1 + t^2), sn = t cs); U^H A U has a
 // zero (p, q) entry.
 __global__ void __launch_bounds__(32 * EV_WARPS)
-ev_cluster_jacobi_kernel(int k, double2* __restrict__ S, double2* __restrict__ M,
-                         const int* __restrict__ perm, const int2* __restrict__ clist,
-                         const EvCtl* __restrict__ ctl, double2* __restrict__ W,
+ev_cluster_jacobi_kernel(int k, const double2* __restrict__ S, const int* __restrict__ perm,
+                         const int2* __restrict__ clist, const EvCtl* __restrict__ ctl,
                          double2* __restrict__ Vstore) {
   extern __shared__ double2 ev_sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -302,19 +325,55 @@ ev_cluster_jacobi_kernel(int k, double2* __restrict__ S, double2* __restrict__ M
       }
     }
   }
-  // store V for the row update, then the column updates (A is free now)
   double2* vs = Vstore + (size_t)ci * EV_CHUNK * EV_CHUNK;
   for (int q = 0; q < m; ++q)
     if (lane < m) vs[q * EV_CHUNK + lane] = V[q * EV_LD + lane];
-  apply_right(k, W, cidx, m, V, A, lane);
-  apply_right(k, S, cidx, m, V, A, lane);
-  apply_right(k, M, cidx, m, V, A, lane);
 }
 
-// Rows of the cluster blocks: Y[c, :] <- V^H Y[c, :] for Y = S and M (after
-// ev_cluster_jacobi multiplied their columns), so that S and M become
-// V^H S V and V^H M V with V block-diagonal.  One warp per cluster block,
-// lanes over columns.
+// Y[r, c] <- sum_p Y[r, c_p] V[p][q] for Y = W, S, M and the rows r of this
+// CTA's slice (blockIdx.y): one warp per cluster block, rows in groups of 32
+// staged through shared memory.
+__global__ void __launch_bounds__(32 * EV_WARPS)
+ev_cluster_cols_kernel(int k, double2* __restrict__ W, double2* __restrict__ S,
+                       double2* __restrict__ M, const int* __restrict__ perm,
+                       const int2* __restrict__ clist, const EvCtl* __restrict__ ctl,
+                       const double2* __restrict__ Vstore) {
+  extern __shared__ double2 ev_sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ci = blockIdx.x * EV_WARPS + warp;
+  if (ci >= ctl->n_clusters) return;
+  const int2 cl = clist[ci];
+  const int a0 = cl.x, m = cl.y;
+  double2* T = ev_sm + (size_t)warp * 2 * EV_CHUNK * EV_LD;  // T[lane][p] at T[lane * EV_LD + p]
+  double2* V = T + EV_CHUNK * EV_LD;                         // V[p][q] at V[q * EV_LD + p]
+  int* cidx = (int*)(ev_sm + (size_t)EV_WARPS * 2 * EV_CHUNK * EV_LD) + warp * EV_CHUNK;
+  const double2* vs = Vstore + (size_t)ci * EV_CHUNK * EV_CHUNK;
+  if (lane < m) cidx[lane] = perm[a0 + lane];
+  for (int q = 0; q < m; ++q)
+    if (lane < m) V[q * EV_LD + lane] = vs[q * EV_CHUNK + lane];
+  const int r_begin = blockIdx.y * EV_ROWS, r_end = min(k, r_begin + EV_ROWS);
+  for (int mat = 0; mat < 3; ++mat) {
+    double2* Y = mat == 0 ? W : (mat == 1 ? S : M);
+    for (int r0 = r_begin; r0 < r_end; r0 += 32) {
+      const int r = r0 + lane;
+      __syncwarp();
+      if (r < r_end)
+        for (int p = 0; p < m; ++p) T[lane * EV_LD + p] = Y[(size_t)cidx[p] * k + r];
+      __syncwarp();
+      if (r < r_end)
+        for (int q = 0; q < m; ++q) {
+          double2 acc = make_double2(0.0, 0.0);
+          for (int p = 0; p < m; ++p) acc = cadd(acc, cmul(T[lane * EV_LD + p], V[q * EV_LD + p]));
+          Y[(size_t)cidx[q] * k + r] = acc;
+        }
+    }
+  }
+}
+
+// Rows of the cluster blocks: Y[c, j] <- (V^H Y[c, :])_j for Y = S and M and
+// the columns j of this CTA's slice (blockIdx.y), after ev_cluster_cols
+// multiplied their columns: S and M become V^H S V and V^H M V with V
+// block-diagonal.  One warp per cluster block, lanes over columns.
 __global__ void __launch_bounds__(32 * EV_WARPS)
 ev_cluster_rows_kernel(int k, double2* __restrict__ S, double2* __restrict__ M,
                        const int* __restrict__ perm, const int2* __restrict__ clist,
@@ -333,15 +392,16 @@ ev_cluster_rows_kernel(int k, double2* __restrict__ S, double2* __restrict__ M,
   for (int q = 0; q < m; ++q)
     if (lane < m) V[q * EV_LD + lane] = vs[q * EV_CHUNK + lane];
   __syncwarp();
+  const int j_begin = blockIdx.y * EV_ROWS, j_end = min(k, j_begin + EV_ROWS);
   for (int mat = 0; mat < 2; ++mat) {
     double2* Y = mat == 0 ? S : M;
-    for (int j0 = 0; j0 < k; j0 += 32) {
+    for (int j0 = j_begin; j0 < j_end; j0 += 32) {
       const int j = j0 + lane;
       __syncwarp();
-      if (j < k)
+      if (j < j_end)
         for (int p = 0; p < m; ++p) T[lane * EV_LD + p] = Y[(size_t)j * k + cidx[p]];
       __syncwarp();
-      if (j < k)
+      if (j < j_end)
         for (int q = 0; q < m; ++q) {
           double2 acc = make_double2(0.0, 0.0);
           for (int p = 0; p < m; ++p) {
@@ -420,6 +480,7 @@ void reduced_eigh_mixed(chfsi_ctx* ctx, int k, double2* G, double* w) {
   int* perm = (int*)ws_get(ctx, "eig_perm", sizeof(int) * k);
   int* pos = (int*)ws_get(ctx, "eig_pos", sizeof(int) * k);
   int* reach = (int*)ws_get(ctx, "eig_reach", sizeof(int) * k);
+  unsigned char* link = (unsigned char*)ws_get(ctx, "eig_link", (size_t)k);
   int2* clist = (int2*)ws_get(ctx, "eig_clist", sizeof(int2) * (k / 2 + 1));
   EvCtl* ctl = (EvCtl*)ws_get(ctx, "eig_ctl", sizeof(EvCtl));
   EvCtl* ctl_h = (EvCtl*)pinned_get(ctx, 256);
@@ -427,6 +488,7 @@ void reduced_eigh_mixed(chfsi_ctx* ctx, int k, double2* G, double* w) {
 
   // S, M of the current W, lam, sorted order and the hard-pair analysis.
   auto analyze = [&]() -> EvHost {
+    const int slot = kt_begin(st);
     CHFSI_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(EvCtl), st));
     CHFSI_CUDA_TRY(cudaMemsetAsync(reach, 0, sizeof(int) * k, st));
     ev_diag_kernel<<<g1, 256, 0, st>>>(k, S, M, lam, ctl);
@@ -436,8 +498,9 @@ void reduced_eigh_mixed(chfsi_ctx* ctx, int k, double2* G, double* w) {
     chfsi_check_launch("ev_pos");
     ev_scan_kernel<<<grid_k2(k), 256, 0, st>>>(k, S, M, lam, pos, ctl, reach);
     chfsi_check_launch("ev_scan");
-    ev_clusters_kernel<<<1, 32, 0, st>>>(k, reach, ctl, clist);
+    ev_clusters_kernel<<<1, EVC_T, 0, st>>>(k, reach, link, ctl, clist);
     chfsi_check_launch("ev_clusters");
+    kt_end(st, slot, KT_EIGCTL, 0.0);
     CHFSI_CUDA_TRY(cudaMemcpyAsync(ctl_h, ctl, sizeof(EvCtl), cudaMemcpyDeviceToHost, st));
     CHFSI_CUDA_TRY(cudaStreamSynchronize(st));
     EvHost h;
@@ -494,6 +557,9 @@ void reduced_eigh_mixed(chfsi_ctx* ctx, int k, double2* G, double* w) {
     CHFSI_CUDA_TRY(cudaFuncSetAttribute(ev_cluster_jacobi_kernel,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)cl_smem));
+    CHFSI_CUDA_TRY(cudaFuncSetAttribute(ev_cluster_cols_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)cl_smem));
     CHFSI_CUDA_TRY(cudaFuncSetAttribute(ev_cluster_rows_kernel,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)cl_smem));
@@ -511,7 +577,7 @@ void reduced_eigh_mixed(chfsi_ctx* ctx, int k, double2* G, double* w) {
     if (!std::isfinite(h.off) || !std::isfinite(h.gnorm))
       throw ChfsiError{CHFSI_ENAN, "reduced eigensolve: non-finite Rayleigh quotient"};
     if (h.off <= EV_ETA * h.gnorm && h.dm <= EV_ORTH) break;
-    if (identity && !tried_fp32 && (h.n_out > 0 || h.max_cluster > 2 * EV_CHUNK)) {
+    if (identity && !tried_fp32 && (h.n_out > 0 || h.max_cluster > EV_SMALL)) {
       fp32_start();
       identity = false;
       tried_fp32 = true;
@@ -526,13 +592,19 @@ void reduced_eigh_mixed(chfsi_ctx* ctx, int k, double2* G, double* w) {
     if (h.n_clusters > 0 && cluster_steps < EV_MAX_CLUSTER_STEPS) {
       // exact rotations of the hard clusters; S and M follow the rotation
       const unsigned nb = (unsigned)((h.n_clusters + EV_WARPS - 1) / EV_WARPS);
-      ev_cluster_jacobi_kernel<<<nb, 32 * EV_WARPS, cl_smem, st>>>(k, S, M, perm, clist, ctl, W,
+      const int slot = kt_begin(st);
+      ev_cluster_jacobi_kernel<<<nb, 32 * EV_WARPS, cl_smem, st>>>(k, S, perm, clist, ctl,
                                                                    Vstore);
       chfsi_check_launch("ev_cluster_jacobi");
-      ev_cluster_rows_kernel<<<nb, 32 * EV_WARPS, cl_smem, st>>>(k, S, M, perm, clist, ctl, Vstore);
+      const dim3 g2(nb, (unsigned)((k + EV_ROWS - 1) / EV_ROWS));
+      ev_cluster_cols_kernel<<<g2, 32 * EV_WARPS, cl_smem, st>>>(k, W, S, M, perm, clist, ctl,
+                                                                 Vstore);
+      chfsi_check_launch("ev_cluster_cols");
+      ev_cluster_rows_kernel<<<g2, 32 * EV_WARPS, cl_smem, st>>>(k, S, M, perm, clist, ctl, Vstore);
       chfsi_check_launch("ev_cluster_rows");
       ev_lam_kernel<<<g1, 256, 0, st>>>(k, S, M, lam);
       chfsi_check_launch("ev_lam");
+      kt_end(st, slot, KT_EIGCTL, 0.0);
       ++cluster_steps;
     }
     if (h.off > EV_ETA * h.gnorm) {

@@ -666,22 +666,28 @@ int oz_check_error(chfsi_ctx* ctx) {
 template <int NS>
 static void oz_slice_a_conj(cudaStream_t st, int nrows_S, int lds, const double2* S, int count,
                             const OzOperand& A, const double* mu) {
+  const int slot = kt_begin(st);
   oz_slice_a_conjcols_kernel<NS><<<count, 256, 0, st>>>(nrows_S, lds, S, A.P, A.data, A.stride,
                                                         A.scale, mu);
   chfsi_check_launch("oz_slice_a_conj");
+  kt_end(st, slot, KT_SLICE, 0.0);
 }
 template <int NS>
 static void oz_slice_a_row(cudaStream_t st, int cols, int lds, const double2* S, int count,
                            const OzOperand& A) {
+  const int slot = kt_begin(st);
   oz_slice_a_rows_kernel<NS><<<(count + 31) / 32, 256, 0, st>>>(count, cols, lds, S, A.P, A.data,
                                                                 A.stride, A.scale);
   chfsi_check_launch("oz_slice_a_rows");
+  kt_end(st, slot, KT_SLICE, 0.0);
 }
 template <int NS>
 static void oz_slice_bb(cudaStream_t st, int rows, int ldt, const double2* T, int count,
                         const OzOperand& B) {
+  const int slot = kt_begin(st);
   oz_slice_b_kernel<NS><<<count, 256, 0, st>>>(rows, ldt, T, B.P, B.data, B.stride, B.scale);
   chfsi_check_launch("oz_slice_b");
+  kt_end(st, slot, KT_SLICE, 0.0);
 }
 #define OZ_DISPATCH(ns, fn, ...)          \
   do {                                    \

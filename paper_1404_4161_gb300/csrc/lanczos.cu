@@ -415,11 +415,13 @@ void lanczos_dev(chfsi_ctx* ctx, const double2* H, int n, int steps, unsigned lo
   a.seed = seed;
   CHFSI_CUDA_TRY(cudaMemsetAsync(a.bar, 0, 64, st));
   void* args[] = {&a};
+  const int lz_slot = kt_begin(st);
   CHFSI_CUDA_TRY(cudaLaunchCooperativeKernel((void*)lanczos_persistent_kernel, dim3(G),
                                              dim3(LZ_THREADS), args, smem, st));
   chfsi_check_launch("lanczos_persistent");
   tridiag_bounds_kernel<<<1, 32, 0, st>>>(m, a.ab, a.ab + m, out4_dev, a.flags);
   chfsi_check_launch("tridiag_bounds");
+  kt_end(st, lz_slot, KT_LANCZOS, 0.0);
 }
 
 const int* lanczos_error_word(chfsi_ctx* ctx) {

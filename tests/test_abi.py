@@ -56,3 +56,29 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "LIB", str(tmp_path / "libchfsi_missing.so"))
     with pytest.raises(ImportError):
         _lib.lib()
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes structs of the binding have the header's sizes and field
+    offsets (compiled with the host C compiler, no GPU)."""
+    import ctypes as C
+    from paper_1404_4161_gb300 import _lib
+    structs = {"chfsi_opts": _lib.Opts, "chfsi_stats": _lib.Stats,
+               "chfsi_filter_item": _lib.FilterItem, "chfsi_problem": _lib.Problem}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "chfsi.h"', 'int main(void) {']
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("  return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                  check=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(got[cname]) == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)

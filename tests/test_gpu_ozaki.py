@@ -210,7 +210,7 @@ def test_sequence_warm_rayleigh_ritz():
     Hs, lam2 = config_sequence(cfg2, BASE_SEED + 2200, length=4, n=n, delta=0.0)
     loops = {}
     for wr in (0, 1):
-        s = Chfsi(precision=L.PREC_TC, f64_gemm=L.GEMM_OZAKI, warm_rr=wr)
+        s = Chfsi(precision=L.PREC_TC, f64_gemm=L.GEMM_OZAKI, warm_rr=wr, warm_resid=0)
         Xc = to_dev_cm(random_block(n, nev + nex, BASE_SEED + 2600))
         ev, sts, rc = s.solve_sequence([to_dev_cm(h) for h in Hs], nev, nex, Xc, 1e-10)
         s.close()
@@ -224,3 +224,32 @@ def test_sequence_warm_rayleigh_ritz():
         loops[wr] = [t["loops"] for t in sts]
     print("loops without / with warm RR", loops)
     assert sum(loops[1][1:]) < sum(loops[0][1:])
+
+
+def test_sequence_warm_residual_start():
+    """opts.warm_resid: on each warm start the residuals of the starting block
+    on the new H (one product, no reduced eigensolve) give the first loop
+    per-vector degrees and the refinement form: same eigenpairs, no more
+    loops than the uniform first-loop degree."""
+    from paper_1404_4161_gb300.build import build
+    build()
+    cfg2 = WORKLOADS["seq10_n4096"]
+    n, nev, nex = 1024, 64, 16
+    Hs, lam2 = config_sequence(cfg2, BASE_SEED + 2200, length=4, n=n, delta=0.0)
+    loops = {}
+    for wr in (0, 1):
+        s = Chfsi(precision=L.PREC_TC, f64_gemm=L.GEMM_OZAKI, warm_resid=wr)
+        Xc = to_dev_cm(random_block(n, nev + nex, BASE_SEED + 2600))
+        ev, sts, rc = s.solve_sequence([to_dev_cm(h) for h in Hs], nev, nex, Xc, 1e-10)
+        s.close()
+        assert rc == L.OK
+        ev = ev.cpu().numpy()
+        for l in range(4):
+            assert np.abs(ev[l, :nev] - lam2[:nev]).max() <= 1e-12 * np.abs(lam2).max()
+        X = from_dev_cm(Xc)
+        R = np.linalg.norm(Hs[-1] @ X[:, :nev] - X[:, :nev] * ev[-1, :nev], axis=0)
+        assert R.max() / np.abs(lam2).max() <= 1e-10
+        assert np.abs(X.conj().T @ X - np.eye(nev + nex)).max() < 1e-12
+        loops[wr] = [t["loops"] for t in sts]
+    print("loops with uniform / residual-based first-loop degrees", loops)
+    assert sum(loops[1][1:]) <= sum(loops[0][1:])
