@@ -413,6 +413,7 @@ def main():
     k64_ms, k64_fl, k64_fx, k64_n = (tot("k_f64_ms"), tot("k_f64_flops"),
                                      tot("k_f64_exec_flops"), tot("k_f64_launches"))
     ktc_ms, ktc_fl, ktc_n = tot("k_tc_ms"), tot("k_tc_flops"), tot("k_tc_launches")
+    ktc_fx = tot("k_tc_exec_flops")
     FP64_PEAK = 1.10  # TFLOP/s, cuBLAS FP64 GEMM on this GB300 (python -m paper_1404_4161_gb300.peaks)
     bf16_peak = peaks.get("bf16_tflops_sustained", 1700.0)
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
@@ -435,12 +436,13 @@ def main():
                                     "MEASURED_PEAKS.json)")}
     tc_roof = None
     if ktc_ms > 0:
-        a = 3.0 * ktc_fl / (ktc_ms / 1e3) / 1e12  # three BF16 products per complex product
+        a = ktc_fx / (ktc_ms / 1e3) / 1e12  # 3 or 6 BF16 products per complex product
         tc_roof = {"bound": "tensor", "achieved": a, "peak": bf16_peak, "unit": "TFLOP/s",
                    "frac": a / bf16_peak, "traffic": TC_FILTER_TRAFFIC.get(n),
                    "traffic_note": TC_FILTER_TRAFFIC_NOTE,
                    "useful_tflops": ktc_fl / (ktc_ms / 1e3) / 1e12,
-                   "kernel": "tc_filter_step_kernel (BF16x3 tcgen05, fused recurrence)",
+                   "kernel": "tc_filter_kernel (persistent, all steps of a filter call in "
+                             "one launch; BF16x3 / BF16x6 tcgen05, fused recurrence)",
                    "launches": int(ktc_n), "avg_launch_ms": ktc_ms / max(ktc_n, 1),
                    "peak_source": "bf16_tflops_sustained of measured"}
     lz_ms = tot("k_lanczos_ms")

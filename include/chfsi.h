@@ -56,9 +56,16 @@ extern "C" {
                             /* residual block (chfsi_filter_refine), so its  */
                             /* error scales with the residual: no FP64 sweep */
 
-/* Split format of the tensor-core filter (CHFSI_PREC_MIXED). */
-#define CHFSI_SPLIT_BF16X3 0 /* x = hi + lo in bf16; hi*hi + hi*lo + lo*hi   */
-#define CHFSI_SPLIT_FP16X3 1 /* same with fp16 and a power-of-two scaling    */
+/* Split format of the tensor-core filter (CHFSI_PREC_MIXED / _TC): each
+ * operand x = x0 + x1 + x2 in bf16 pieces (x0 = bf16(x), x1 = bf16(x - x0),
+ * x2 = bf16(x - x0 - x1)), FP32 accumulation in TMEM. */
+#define CHFSI_SPLIT_BF16X3 0 /* x0 y0 + x0 y1 + x1 y0: 3 products, ~2^-16     */
+#define CHFSI_SPLIT_BF16X6 1 /* adds x0 y2 + x1 y1 + x2 y0: 6 products,       */
+                             /* ~2^-20 (the FP32 accumulation dominates)    */
+#define CHFSI_SPLIT_ADAPTIVE 2 /* the solver uses BF16X6 for the refinement  */
+                             /* form while 2^-16 x 1.7 x the largest wanted */
+                             /* residual exceeds tol/3, else BF16X3; the     */
+                             /* single-step entry points use BF16X3         */
 
 /* Engine of the FP64 products (H Q, Gram matrices, block products). */
 #define CHFSI_GEMM_FP64 0   /* DFMA kernels on the FP64 pipe                 */
@@ -75,7 +82,7 @@ typedef struct chfsi_ctx chfsi_ctx;
 
 typedef struct chfsi_opts {
   int precision;       /* CHFSI_PREC_FP64 / _MIXED / _TC      (FP64)       */
-  int split;           /* CHFSI_SPLIT_*                       (BF16X3)     */
+  int split;           /* CHFSI_SPLIT_*                       (ADAPTIVE)   */
   int degree_model;    /* CHFSI_DEG_*                         (ANALYTIC)   */
   int deg_cold;        /* first-loop degree, random start     (20)         */
   int deg_warm;        /* first-loop degree, warm start       (8)          */
@@ -143,6 +150,8 @@ typedef struct chfsi_stats {
   double k_slice_ms;        /* operand slicers of the tensor-core engine */
   double k_eigctl_ms;       /* control kernels of the reduced eigensolve */
                             /* (analysis, cluster rotations)             */
+  double k_tc_exec_flops;   /* flops the tensor-core filter executed: 3 or */
+                            /* 6 BF16 products per complex product         */
 } chfsi_stats;
 
 /* ---- context ---------------------------------------------------------- */

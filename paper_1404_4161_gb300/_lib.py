@@ -14,7 +14,7 @@ from .build import LIB
 OK, EINVAL, ENOMEM, ENOCONV, EBREAKDOWN, ENAN, ETIMEOUT, ECUDA, ENOTSUP, ETOOBIG = range(10)
 FILTER_STATIC_MAX_NK = 262144
 PREC_FP64, PREC_MIXED, PREC_TC = 0, 1, 2
-SPLIT_BF16X3, SPLIT_FP16X3 = 0, 1
+SPLIT_BF16X3, SPLIT_BF16X6, SPLIT_ADAPTIVE = 0, 1, 2
 DEG_ANALYTIC, DEG_MLP = 0, 1
 GEMM_FP64, GEMM_OZAKI = 0, 1
 MLP_NPARAM = 64 * 5 + 64 + 64 * 64 + 64 + 64 + 1
@@ -44,7 +44,7 @@ class Stats(C.Structure):
                 ("loops_mlp", C.c_int), ("mlp_fallback", C.c_int),
                 ("k_f64_exec_flops", C.c_double), ("k_cholinv_ms", C.c_double),
                 ("k_lanczos_ms", C.c_double), ("k_slice_ms", C.c_double),
-                ("k_eigctl_ms", C.c_double)]
+                ("k_eigctl_ms", C.c_double), ("k_tc_exec_flops", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -115,7 +115,9 @@ void validate_opts(const chfsi_opts& o) {
   CHFSI_REQUIRE(o.precision == CHFSI_PREC_FP64 || o.precision == CHFSI_PREC_MIXED ||
                     o.precision == CHFSI_PREC_TC,
                 "opts.precision");
-  CHFSI_REQUIRE(o.split == CHFSI_SPLIT_BF16X3 || o.split == CHFSI_SPLIT_FP16X3, "opts.split");
+  CHFSI_REQUIRE(o.split == CHFSI_SPLIT_BF16X3 || o.split == CHFSI_SPLIT_BF16X6 ||
+                    o.split == CHFSI_SPLIT_ADAPTIVE,
+                "opts.split");
   CHFSI_REQUIRE(o.degree_model == CHFSI_DEG_ANALYTIC || o.degree_model == CHFSI_DEG_MLP,
                 "opts.degree_model");
   CHFSI_REQUIRE(o.deg_min >= 1 && o.deg_max >= o.deg_min && o.deg_max <= 512,
@@ -437,6 +439,7 @@ struct Problem {
   double* psi = nullptr;  // refinement tables of the current loop
   double* fR = nullptr;
   bool h_sliced = false;  // tensor-core slices of H built for this problem
+  int slot = 0;           // operand slot of the tensor-core filter
   bool have_R = false;    // residual block of the current Ritz pairs built
 
   void* ws(const char* name, size_t bytes) { return ws_get(ctx, (pre + name).c_str(), bytes); }
@@ -524,6 +527,9 @@ struct Problem {
       throw ChfsiError{CHFSI_ENAN, "Lanczos bounds are not finite"};
     S.beta = beta;
     S.norm_h = norm_h;
+    // split pieces of H for the tensor-core filter, once per problem
+    if (mixed || tc_all)
+      tc_filter_prepare(ctx, slot, H, n, o->split == CHFSI_SPLIT_BF16X3 ? 2 : 3);
     int deg0;
     if (warm) {
       warm_start = true;
@@ -608,15 +614,25 @@ struct Problem {
     return F64;
   }
 
+  // bf16 pieces of the tensor-core filter in this loop.  Adaptive: the
+  // refinement form's error is about 2^-16 x 1.7 times the residual with two
+  // pieces (3 products); three pieces (6 products) while that would not
+  // stay below a third of tol.
+  int split_pieces(FilterKind kind) const {
+    if (o->split == CHFSI_SPLIT_BF16X3) return 2;
+    if (o->split == CHFSI_SPLIT_BF16X6) return 3;
+    return (kind == TC_DEFECT && max_resid_wanted * 1.7 * 0x1p-16 > tol / 3.0) ? 3 : 2;
+  }
+
   // The filter of this loop run by this problem alone.
   void filter_single(FilterKind kind) {
-    if (kind == TC_PLAIN)
-      tc_filter_run(ctx, H, n, ka, Xact, degs.data(), gamma, c_(), e_(), Yf);
-    else if (kind == TC_DEFECT)
-      tc_filter_run_defect(ctx, H, n, ka, Xact, Rblk, lam_act, degs.data(), deg_sorted, gamma,
-                           c_(), e_(), Yf);
-    else
+    if (kind == F64) {
       filter_f64(ctx, H, n, ka, Xact, degs.data(), gamma, c_(), e_(), Yf);
+      return;
+    }
+    TcBatchItem it = batch_item(kind);
+    tc_filter_launch(ctx, 1, &it, split_pieces(kind));
+    after_batch(kind);
   }
 
   // Work item of this loop's filter for a batched launch.
@@ -633,6 +649,8 @@ struct Problem {
     it.c = c_();
     it.e = e_();
     it.out = Yf;
+    it.slot = slot;
+    it.h_ready = true;
     if (kind == TC_DEFECT) {
       tc_defect_tables(ctx, pre, ka, lam_act, degs.data(), gamma, c_(), e_(), &psi, &fR);
       it.R = Rblk;
@@ -803,6 +821,7 @@ void copy_kernel_times(chfsi_stats& S, const KernelTimer& t) {
   S.k_lanczos_ms = t.ms[KT_LANCZOS];
   S.k_slice_ms = t.ms[KT_SLICE];
   S.k_eigctl_ms = t.ms[KT_EIGCTL];
+  S.k_tc_exec_flops = t.fx[KT_TC];
 }
 
 struct TimerScope {
@@ -847,9 +866,11 @@ int solve_batch(chfsi_ctx* ctx, int P, const double2* const* H, const int* n, co
   KernelTimer timer;
   TimerScope scope(ctx->opts.profile ? &timer : nullptr);
   std::vector<Problem> pbs(P);
-  for (int p = 0; p < P; ++p)
+  for (int p = 0; p < P; ++p) {
+    pbs[p].slot = p;
     pbs[p].init(ctx, "b" + std::to_string(p) + ".", H[p], n[p], nev[p], nex[p], X[p], tol,
                 evals[p], warm ? warm + 2 * p : nullptr, stats ? stats + p : nullptr, step);
+  }
   cudaEvent_t e0, e1;
   CHFSI_CUDA_TRY(cudaEventCreate(&e0));
   CHFSI_CUDA_TRY(cudaEventCreate(&e1));
@@ -862,15 +883,17 @@ int solve_batch(chfsi_ctx* ctx, int P, const double2* const* H, const int* n, co
     std::vector<Problem::FilterKind> kind(P, Problem::F64);
     std::vector<TcBatchItem> items;
     std::vector<int> in_batch;
+    int ns = 2;
     for (int p : act) {
       kind[p] = pbs[p].begin_loop();
       if (kind[p] != Problem::F64) {
         items.push_back(pbs[p].batch_item(kind[p]));
         in_batch.push_back(p);
+        ns = std::max(ns, pbs[p].split_pieces(kind[p]));
       }
     }
     CHFSI_CUDA_TRY(cudaEventRecord(e0, ctx->stream));
-    if (!items.empty()) tc_filter_batched_run(ctx, (int)items.size(), items.data());
+    if (!items.empty()) tc_filter_launch(ctx, (int)items.size(), items.data(), ns);
     for (int p : in_batch) pbs[p].after_batch(kind[p]);
     for (int p : act)
       if (kind[p] == Problem::F64) pbs[p].filter_single(kind[p]);
@@ -920,7 +943,7 @@ extern "C" {
 void chfsi_default_opts(chfsi_opts* o) {
   if (!o) return;
   o->precision = CHFSI_PREC_FP64;
-  o->split = CHFSI_SPLIT_BF16X3;
+  o->split = CHFSI_SPLIT_ADAPTIVE;
   o->degree_model = CHFSI_DEG_ANALYTIC;
   o->deg_cold = 20;
   o->deg_warm = 8;
@@ -1002,7 +1025,6 @@ void chfsi_free(chfsi_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
   tc_filter_release(ctx);
-  tc_filter_batched_release(ctx);
   mlp_destroy(ctx);
   ws_free_all(ctx);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
@@ -1180,7 +1202,8 @@ int chfsi_filter(chfsi_ctx* ctx, const double* H, int n, int k, const double* Y0
     if (precision == CHFSI_PREC_MIXED || precision == CHFSI_PREC_TC) {
       if (!tc_filter_supported(ctx))
         throw ChfsiError{CHFSI_ENOTSUP, "split-precision filter needs an sm_103 device"};
-      tc_filter_run(ctx, C2(H), n, k, C2(Y0), degrees_host, lam1, c, e, C2(Y));
+      tc_filter_run(ctx, C2(H), n, k, C2(Y0), degrees_host, lam1, c, e, C2(Y),
+                    ctx->opts.split == CHFSI_SPLIT_BF16X6 ? 3 : 2);
     } else {
       CHFSI_REQUIRE(precision == CHFSI_PREC_FP64, "bad precision");
       filter_f64(ctx, C2(H), n, k, C2(Y0), degrees_host, lam1, c, e, C2(Y));
@@ -1219,9 +1242,11 @@ int chfsi_filter_batched(chfsi_ctx* ctx, int P, const chfsi_filter_item* items) 
       b.c = it.c;
       b.e = it.e;
       b.out = C2(it.Y);
+      b.slot = (int)v.size();
+      b.h_ready = false;
       v.push_back(b);
     }
-    tc_filter_batched_run(ctx, (int)v.size(), v.data());
+    tc_filter_launch(ctx, (int)v.size(), v.data(), ctx->opts.split == CHFSI_SPLIT_BF16X6 ? 3 : 2);
   });
 }
 
@@ -1246,7 +1271,7 @@ int chfsi_filter_refine(chfsi_ctx* ctx, const double* H, int n, int k, const dou
     CHFSI_CUDA_TRY(cudaMemcpyAsync(dd, degrees_host, sizeof(int) * k, cudaMemcpyHostToDevice,
                                    ctx->stream));
     tc_filter_run_defect(ctx, C2(H), n, k, C2(Y), C2(R), ritz, degrees_host, dd, lam1, c, e,
-                         C2(Yout));
+                         C2(Yout), ctx->opts.split == CHFSI_SPLIT_BF16X6 ? 3 : 2);
   });
 }
 

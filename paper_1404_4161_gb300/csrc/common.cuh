@@ -211,22 +211,18 @@ void sort_by_degree(cudaStream_t st, int k, const int* deg, const int* idx_or_nu
 void sort_by_value(cudaStream_t st, int k, const double* val, int* perm);
 void degree_cap_buffer(cudaStream_t st, int k, int n_wanted, int* deg);
 
-// Tensor-core split-precision filter (filter_tc.cu).
+// Tensor-core split-precision filter (filter_tc.cu): one persistent launch
+// runs every step of Alg. 2 for one or many problems.  ns = bf16 pieces per
+// operand: 2 (3 products, ~2^-16) or 3 (6 products, ~2^-20 with the FP32
+// accumulation).
 int tc_filter_supported(chfsi_ctx* ctx);
-void tc_filter_prepare(chfsi_ctx* ctx, const double2* H, int n);
-void tc_filter_run(chfsi_ctx* ctx, const double2* H, int n, int k, const double2* Y0,
-                   const int* deg_host, double lam1, double c, double e, double2* Yout);
-void tc_filter_run_defect(chfsi_ctx* ctx, const double2* H, int n, int k, const double2* Y,
-                          const double2* Rres, const double* lam, const int* deg_host,
-                          const int* deg_dev, double lam1, double c, double e, double2* Yout);
-void tc_filter_release(chfsi_ctx* ctx);
-// Launchers of the operand-preparation kernels (filter_tc.cu).
-void tc_repack_h(cudaStream_t st, int n, int P, const double2* H, void* Ah, void* Al);
-void tc_split_block(cudaStream_t st, int n, int k, int P, const double2* src, double scale,
-                    float2* master, void* bh, void* bl, double2* out, int fin_end);
-// One problem of a batched filter launch (filter_batched.cu).  Plain form:
-// src = Y0, R = fR = null.  Refinement form: R = residual block, fR =
-// forcing table ((m_k + 1) x k, row i for step i); out receives D.
+// A pieces of H (n x n) in operand slot `slot` (kept until the slot is
+// prepared again): a solver prepares each problem's H once.
+void tc_filter_prepare(chfsi_ctx* ctx, int slot, const double2* H, int n, int pieces);
+// One problem of a filter launch.  Plain form: src = Y0, R = fR = null.
+// Refinement form: R = residual block, fR = forcing table ((m_k + 1) x k,
+// row i for step i); out receives D.  slot: operand slot of the problem;
+// h_ready: its A pieces are already those of H (tc_filter_prepare).
 struct TcBatchItem {
   const double2* H;
   int n, k;
@@ -236,14 +232,22 @@ struct TcBatchItem {
   const int* deg;  // host, ascending
   double lam1, c, e;
   double2* out;
+  int slot;
+  bool h_ready;
 };
-void tc_filter_batched_run(chfsi_ctx* ctx, int P, const TcBatchItem* items);
+void tc_filter_launch(chfsi_ctx* ctx, int P, const TcBatchItem* items, int ns);
+void tc_filter_run(chfsi_ctx* ctx, const double2* H, int n, int k, const double2* Y0,
+                   const int* deg_host, double lam1, double c, double e, double2* Yout, int ns);
+void tc_filter_run_defect(chfsi_ctx* ctx, const double2* H, int n, int k, const double2* Y,
+                          const double2* Rres, const double* lam, const int* deg_host,
+                          const int* deg_dev, double lam1, double c, double e, double2* Yout,
+                          int ns);
+void tc_filter_release(chfsi_ctx* ctx);
 void tc_defect_tables(chfsi_ctx* ctx, const std::string& prefix, int k, const double* lam,
                       const int* deg_host, double lam1, double c, double e, double** psi,
                       double** fR);
 void tc_defect_combine(cudaStream_t st, int n, int k, const double2* Y, const int* deg_dev,
                        const double* psi, double2* out);
-void tc_filter_batched_release(chfsi_ctx* ctx);
 // R[:, j] = HY[:, perm[j]] - lam[perm[j]] Y[:, perm[j]], lam_out[j] = lam[perm[j]].
 void residual_block(cudaStream_t st, int n, int k, const double2* HY, const double2* Y,
                     const double* lam, const int* perm, double2* R, double* lam_out);

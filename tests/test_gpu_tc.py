@@ -1,5 +1,5 @@
-"""Parity of the split-precision (BF16x3) tensor-core filter with the
-oracle's Alg. 2, through the C ABI.
+"""Parity of the split-precision tensor-core filter (BF16x3, and BF16x6
+with three pieces) with the oracle's Alg. 2, through the C ABI.
 
 Tolerances follow from the arithmetic.  A BF16x3 product keeps about 16
 bits (the dropped lo*lo term and the rounding of lo are both ~2^-16 of
@@ -86,6 +86,37 @@ def test_tc_filter_refine(ctx, n, k, noise):
     print(f"refine n={n} k={k} max err/bound {ratio:.3f}, "
           f"median sum||D_i||/||Y'|| {plain_scale:.2e}, max col rel err {colrel(got, ref):.2e}")
     assert ratio < 1.0
+
+
+@pytest.mark.parametrize("n,degrees", [
+    (777, [1] * 5 + [4] * 40 + [9] * 30 + [17] * 20 + [30]),
+    (1024, list(range(1, 161))),
+])
+def test_tc_filter_six_products(n, degrees):
+    """Three bf16 pieces per operand (6 products): the split error drops to
+    ~2^-23 and what is left is the bias of the tensor cores' FP32
+    accumulation within one K chunk (about 96 accumulates rounding toward
+    zero, ~1.5e-6 relative per product); the bound is m 2^-19 ||Hs|| (4x
+    margin), and the result must be at least 2x closer to the oracle than
+    the 3-product split (whose ~2^-16 split error dominates)."""
+    H, lam, _ = known_problem(n, 100 + n)
+    Y0 = random_block(n, len(degrees), 200 + n)
+    alpha, beta = 0.4, 10.3
+    c, e = 0.5 * (alpha + beta), 0.5 * (beta - alpha)
+    ref = oracle.chebyshev_filter(H, Y0, degrees, lam[0], c, e)
+    errs = {}
+    for split in (L.SPLIT_BF16X3, L.SPLIT_BF16X6):
+        s = Chfsi(split=split)
+        got = from_dev_cm(s.filter(to_dev_cm(H), to_dev_cm(Y0), degrees, lam[0], c, e,
+                                   precision=L.PREC_MIXED))
+        s.close()
+        errs[split] = colrel(got, ref)
+    hs = max(abs(lam[0] - c), abs(lam[-1] - c)) / e
+    lim = 4.0 * max(degrees) * 2.0 ** -19 * max(1.0, hs)
+    print(f"n={n}: 3 products {errs[L.SPLIT_BF16X3]:.2e}, 6 products {errs[L.SPLIT_BF16X6]:.2e}"
+          f" (bound {lim:.2e})")
+    assert errs[L.SPLIT_BF16X6] < lim
+    assert errs[L.SPLIT_BF16X6] * 2 < errs[L.SPLIT_BF16X3]
 
 
 def check(H, lam, X, ev, nev, tol=1e-10):
