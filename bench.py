@@ -469,6 +469,8 @@ def main():
     roof = max(cands, key=lambda r: r["avg_launch_ms"] * r["launches"]) if cands else None
     dominant = max(kernel_ms, key=kernel_ms.get)
 
+    filter_tuning = s.autotune_table()
+
     # end to end: same solve through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -582,6 +584,7 @@ def main():
             "mlp_training": train_info,
             "batched": batched,
             "loops_mlp": [x["loops_mlp"] for x in last],
+            "filter_autotune": filter_tuning,
         }
         print(json.dumps(out))
     s.close()

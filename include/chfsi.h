@@ -109,6 +109,11 @@ typedef struct chfsi_opts {
                        /* already converged lock, the first loop gets     */
                        /* per-vector degrees and (CHFSI_PREC_TC) the      */
                        /* refinement form; 0: the uniform deg_warm (0)    */
+  int autotune;        /* 1: the tensor-core filter times its candidate   */
+                       /* tilings (column block width x tile grouping)    */
+                       /* on the first launch of each (n, k/32, split)    */
+                       /* shape and keeps the fastest for the context;    */
+                       /* results do not depend on the tiling (1)         */
 } chfsi_opts;
 
 /* Per-problem statistics (host struct, filled when non-NULL). */
@@ -323,6 +328,15 @@ int chfsi_residuals(chfsi_ctx* ctx, int n, int k, const double* HY,
  * degree.  ritz, resid: k doubles; degrees: k ints (all device). */
 int chfsi_degrees(chfsi_ctx* ctx, int k, const double* ritz, const double* resid,
                   double c, double e, double tol, int n_wanted, int* degrees);
+
+/* Tilings the autotuner chose in this context (opts.autotune): 6 ints per
+ * entry in entries_host {n, k rounded up to 32, bf16 pieces (2 or 3),
+ * column block width, blocks per tile group, time of the winning trial in
+ * microseconds}; at most max_entries are written, *n_entries_host gets the
+ * total.  The paper has no counterpart: its Sec. 4 tunes the algorithmic
+ * block size and the process grid of the distributed GEMMs by hand. */
+int chfsi_autotune_table(chfsi_ctx* ctx, int max_entries, int* entries_host,
+                         int* n_entries_host);
 
 /* ---- filter without device allocation ---------------------------------- */
 

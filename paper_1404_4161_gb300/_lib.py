@@ -26,7 +26,8 @@ class Opts(C.Structure):
                 ("deg_max", C.c_int), ("deg_extra", C.c_int), ("lanczos_steps", C.c_int),
                 ("max_loops", C.c_int), ("switch_tol", C.c_double), ("seed", C.c_ulonglong),
                 ("profile", C.c_int), ("mlp_extra", C.c_int), ("step0", C.c_int),
-                ("f64_gemm", C.c_int), ("warm_rr", C.c_int), ("warm_resid", C.c_int)]
+                ("f64_gemm", C.c_int), ("warm_rr", C.c_int), ("warm_resid", C.c_int),
+                ("autotune", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -85,6 +86,7 @@ _SIGS = {
                                             C.c_double, _P, _P]),
     "chfsi_solve_batched": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_double, _P]),
     "chfsi_lanczos": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_ulonglong, _P]),
+    "chfsi_autotune_table": (C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_int)]),
     "chfsi_filter": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, C.c_double, C.c_double,
                                C.c_double, _P, C.c_int]),
     "chfsi_filter_batched": (C.c_int, [_P, C.c_int, _P]),

@@ -130,6 +130,7 @@ void validate_opts(const chfsi_opts& o) {
   CHFSI_REQUIRE(o.mlp_extra >= 0 && o.step0 >= 0, "opts.mlp_extra/step0");
   CHFSI_REQUIRE((o.warm_rr == 0 || o.warm_rr == 1) && (o.warm_resid == 0 || o.warm_resid == 1),
                 "opts.warm_rr/warm_resid");
+  CHFSI_REQUIRE(o.autotune == 0 || o.autotune == 1, "opts.autotune");
   CHFSI_REQUIRE(o.f64_gemm == CHFSI_GEMM_FP64 || o.f64_gemm == CHFSI_GEMM_OZAKI,
                 "opts.f64_gemm");
 }
@@ -960,6 +961,7 @@ void chfsi_default_opts(chfsi_opts* o) {
   o->f64_gemm = CHFSI_GEMM_FP64;
   o->warm_rr = 0;
   o->warm_resid = 0;
+  o->autotune = 1;
 }
 
 const char* chfsi_strerror(int code) {
@@ -1164,6 +1166,15 @@ int chfsi_solve_batched(chfsi_ctx* ctx, int P, const chfsi_problem* probs, int s
     }
   });
   return rc != CHFSI_OK ? rc : status;
+}
+
+int chfsi_autotune_table(chfsi_ctx* ctx, int max_entries, int* entries_host,
+                         int* n_entries_host) {
+  if (!ctx || !n_entries_host || max_entries < 0) return CHFSI_EINVAL;
+  return run_guarded(ctx, [&] {
+    CHFSI_REQUIRE(max_entries == 0 || entries_host, "bad table buffer");
+    *n_entries_host = tc_tuning_table(ctx, max_entries, entries_host);
+  });
 }
 
 int chfsi_lanczos(chfsi_ctx* ctx, const double* H, int n, int steps, unsigned long long seed,

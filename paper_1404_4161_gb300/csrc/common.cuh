@@ -236,6 +236,9 @@ struct TcBatchItem {
   bool h_ready;
 };
 void tc_filter_launch(chfsi_ctx* ctx, int P, const TcBatchItem* items, int ns);
+// Autotuned tilings of this context: 6 ints per entry {n, k bucket (k rounded
+// up to 32), pieces, block width, group, microseconds}; returns the count.
+int tc_tuning_table(chfsi_ctx* ctx, int max_entries, int* out);
 void tc_filter_run(chfsi_ctx* ctx, const double2* H, int n, int k, const double2* Y0,
                    const int* deg_host, double lam1, double c, double e, double2* Yout, int ns);
 void tc_filter_run_defect(chfsi_ctx* ctx, const double2* H, int n, int k, const double2* Y,

@@ -40,8 +40,11 @@
 //   * A "segment" is one step of one problem; segments are ordered by
 //     (step, problem).  The columns of a problem are cut into blocks of N
 //     real columns at fixed positions (block b = columns [bN, (b+1)N)); a
-//     segment's tiles are (block, row tile) pairs, block-major, and a tile
-//     covers the part of its block that is still active at that step.
+//     segment's tiles are (block, row tile) pairs and a tile covers the
+//     part of its block that is still active at that step.  Blocks are
+//     taken in groups of up to (SMs / row tiles), row-tile-major inside a
+//     group, so that the tiles sharing a row tile of A run side by side and
+//     read it from L2 once.
 //   * Output tile (m, b) of step i+1 reads the whole of Y_i's block b, so
 //     it waits until every row tile of block b of step i is published (a
 //     per-(segment, block) counter).  Steps therefore overlap: the blocks
@@ -67,6 +70,7 @@
 //                  warp's release add on the (segment, block) counter.
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -90,6 +94,7 @@ struct FProb {
 
 struct FSeg {
   int p, step, tile_base, mt, blk0, nblk;
+  int grp;              // blocks per tile group (row-tile-major inside a group)
   int s_col, s_new;     // first active column; columns below s_new finish here
   float a, b, c;
   int cur, prev, next;  // master indices; prev < 0 when b == 0
@@ -155,11 +160,17 @@ __device__ __forceinline__ int find_seg(const FSeg* segs, int nsegs, int t) {
 struct TileGeo {
   int m0, bi, cs, ce;  // row start, block within the segment, real column range [cs, ce)
 };
+// Tiles of a segment: blocks in groups of sg.grp; inside a group, row tile
+// major (the blocks of one row tile are consecutive, so the CTAs holding
+// them run side by side and read the same A K blocks from L2).
 __device__ __forceinline__ TileGeo tile_geo(const FSeg& sg, const FProb& pr, int t) {
   TileGeo g;
   const int local = t - sg.tile_base;
-  g.bi = local / sg.mt;
-  g.m0 = (local % sg.mt) * BM;
+  const int gi = local / (sg.mt * sg.grp);
+  const int rem = local - gi * sg.mt * sg.grp;
+  const int gsz = min(sg.grp, sg.nblk - gi * sg.grp);
+  g.bi = gi * sg.grp + rem % gsz;
+  g.m0 = (rem / gsz) * BM;
   const int b = sg.blk0 + g.bi;
   g.cs = max(b * pr.ntile, 2 * sg.s_col);
   g.ce = min((b + 1) * pr.ntile, 2 * pr.k);
@@ -569,8 +580,20 @@ struct TcSlot {
   float2* Rf = nullptr;        // n x kcap
 };
 
+// Tiling of a launch: block width N (real columns) and blocks per tile
+// group; 0 = the rule (block_width, SMs / row tiles).
+struct TcTiling {
+  int N = 0, G = 0;
+};
+
+struct TcTuned {
+  TcTiling t;
+  float us = 0.f;
+};
+
 struct TcFilterState {
   std::vector<TcSlot> slots;
+  std::map<unsigned long long, TcTuned> tuned;  // (n, k / 32, pieces) -> best tiling
   FProb* d_probs = nullptr;
   FSeg* d_segs = nullptr;
   CUtensorMap* d_maps = nullptr;
@@ -655,9 +678,8 @@ void tc_filter_prepare(chfsi_ctx* ctx, int slot, const double2* H, int n, int pi
   sl.pieces = pieces;
 }
 
-void tc_filter_launch(chfsi_ctx* ctx, int P, const TcBatchItem* items, int ns) {
-  if (P <= 0) return;
-  CHFSI_REQUIRE(ns == 2 || ns == 3, "split pieces must be 2 or 3");
+static void launch_with(chfsi_ctx* ctx, int P, const TcBatchItem* items, int ns,
+                        const TcTiling& tl) {
   TcFilterState* fs = tc_state(ctx);
   cudaStream_t st = ctx->stream;
   std::vector<FProb> probs(P);
@@ -676,7 +698,7 @@ void tc_filter_launch(chfsi_ctx* ctx, int P, const TcBatchItem* items, int ns) {
     pr.k = k;
     pr.P = sl.P;
     pr.kblocks = (2 * n + BK - 1) / BK;
-    pr.ntile = block_width(k);
+    pr.ntile = tl.N > 0 ? std::min(tl.N, (2 * k + 15) / 16 * 16) : block_width(k);
     pr.M = sl.M;
     pr.B = sl.B;
     pr.b_elems = (long long)b_el;
@@ -748,6 +770,9 @@ void tc_filter_launch(chfsi_ctx* ctx, int P, const TcBatchItem* items, int ns) {
       sg.mt = (it.n + BM - 1) / BM;
       sg.blk0 = (2 * s) / N;
       sg.nblk = (2 * k + N - 1) / N - sg.blk0;
+      // as many blocks per group as keep one group's tiles within the CTAs
+      sg.grp = tl.G > 0 ? std::min(tl.G, sg.nblk)
+                        : std::max(1, std::min(sg.nblk, ctx->sm_count / sg.mt));
       sg.tile_base = tiles;
       sg.done_base = counters;
       if (last_seg[p] >= 0) {
@@ -820,6 +845,84 @@ void tc_filter_launch(chfsi_ctx* ctx, int P, const TcBatchItem* items, int ns) {
   if (*h)
     throw ChfsiError{CHFSI_ETIMEOUT, "tensor-core filter: a bounded wait gave up (code " +
                                          std::to_string(*h) + ")"};
+}
+
+// Filter launch with a measured tiling (the autotuner, opts.autotune): the
+// block width N and the group size decide only which CTA computes which
+// output tile; every output element sums the same products in the same K
+// order, so all tilings give identical results.  The first single-problem
+// launch of each (n, k / 32, pieces) shape times every candidate once (the
+// launch is idempotent: it rebuilds its state from Y0 or R), keeps the
+// fastest for the context and then runs it; later launches of that shape use
+// it directly.  Batched launches use the rule.
+void tc_filter_launch(chfsi_ctx* ctx, int P, const TcBatchItem* items, int ns) {
+  if (P <= 0) return;
+  CHFSI_REQUIRE(ns == 2 || ns == 3, "split pieces must be 2 or 3");
+  TcFilterState* fs = tc_state(ctx);
+  TcTiling tl;
+  if (P == 1 && ctx->opts.autotune) {
+    const unsigned long long key = ((unsigned long long)items[0].n << 32) |
+                                   ((unsigned long long)((items[0].k + 31) / 32) << 8) |
+                                   (unsigned long long)ns;
+    auto it = fs->tuned.find(key);
+    if (it == fs->tuned.end()) {
+      cudaStream_t st = ctx->stream;
+      KernelTimer* saved = kt_current();
+      kt_install(nullptr);  // the trials are not part of the solve's kernel times
+      cudaEvent_t e0, e1;
+      CHFSI_CUDA_TRY(cudaEventCreate(&e0));
+      CHFSI_CUDA_TRY(cudaEventCreate(&e1));
+      TcTuned best;
+      best.us = 1e30f;
+      try {
+        launch_with(ctx, P, items, ns, TcTiling{});  // warm-up (slot buffers, first use)
+        for (int N : {64, 96, 128})
+          for (int G : {1, 2, 4}) {
+            if (N > (2 * items[0].k + 15) / 16 * 16 + 15) continue;
+            TcTiling cand{N, G};
+            CHFSI_CUDA_TRY(cudaEventRecord(e0, st));
+            launch_with(ctx, P, items, ns, cand);
+            CHFSI_CUDA_TRY(cudaEventRecord(e1, st));
+            CHFSI_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CHFSI_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (1e3f * ms < best.us) {
+              best.us = 1e3f * ms;
+              best.t = cand;
+            }
+          }
+      } catch (...) {
+        kt_install(saved);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+      }
+      kt_install(saved);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      it = fs->tuned.emplace(key, best).first;
+    }
+    tl = it->second.t;
+  }
+  launch_with(ctx, P, items, ns, tl);
+}
+
+int tc_tuning_table(chfsi_ctx* ctx, int max_entries, int* out) {
+  TcFilterState* fs = tc_state(ctx);
+  int n = 0;
+  for (const auto& kv : fs->tuned) {
+    if (n < max_entries && out) {
+      int* e = out + 6 * n;
+      e[0] = (int)(kv.first >> 32);
+      e[1] = (int)((kv.first >> 8) & 0xFFFFFFu) * 32;
+      e[2] = (int)(kv.first & 0xFF);
+      e[3] = kv.second.t.N;
+      e[4] = kv.second.t.G;
+      e[5] = (int)kv.second.us;
+    }
+    ++n;
+  }
+  return n;
 }
 
 // Refinement-form tables for one problem: psi[i][j] = psi_i(lambda_j) and

@@ -197,6 +197,17 @@ class Chfsi:
                                            n_wanted, _ptr(d)))
         return d
 
+    def autotune_table(self):
+        """Tilings chosen by the filter's autotuner: list of dicts."""
+        cnt = C.c_int()
+        self._check(self.lib.chfsi_autotune_table(self.ctx, 0, None, C.byref(cnt)))
+        n = cnt.value
+        buf = (C.c_int * max(6 * n, 1))()
+        self._check(self.lib.chfsi_autotune_table(self.ctx, n, C.cast(buf, C.c_void_p),
+                                                  C.byref(cnt)))
+        keys = ["n", "k_bucket", "pieces", "block_width", "group", "us"]
+        return [dict(zip(keys, buf[6 * i:6 * i + 6])) for i in range(n)]
+
     # -- traces and MLP ------------------------------------------------
     def trace_enable(self, capacity_rows):
         self._check(self.lib.chfsi_trace_enable(self.ctx, int(capacity_rows)))

@@ -159,3 +159,30 @@ def test_sequence_tensor_core_known_spectrum():
         assert st["status"] == L.OK and st["loops_lowp"] == st["loops"]
         assert np.abs(ev[l, :nev] - lam[:nev]).max() <= 1e-12 * np.abs(lam).max()
     check(Hs[-1], lam, from_dev_cm(Xc), ev[-1], nev)
+
+
+def test_autotuned_tiling_gives_identical_results():
+    """The filter's autotuner only changes which CTA computes which tile:
+    with and without it the output is bit-identical, and the table lists
+    the tuned shape (n, k rounded up to 32, 2 pieces) with a candidate
+    tiling."""
+    n, k = 1000, 97
+    H, lam, _ = known_problem(n, 4242)
+    Y0 = random_block(n, k, 4243)
+    degrees = sorted(np.random.Generator(np.random.PCG64(5)).integers(1, 12, k))
+    c, e = 5.35, 4.95
+    outs = {}
+    for tune in (0, 1):
+        s = Chfsi(autotune=tune, split=L.SPLIT_BF16X3)
+        outs[tune] = s.filter(to_dev_cm(H), to_dev_cm(Y0), degrees, lam[0], c, e,
+                              precision=L.PREC_MIXED).cpu().numpy()
+        table = s.autotune_table()
+        s.close()
+        if tune:
+            assert len(table) == 1
+            t = table[0]
+            assert (t["n"], t["k_bucket"], t["pieces"]) == (n, 128, 2)
+            assert t["block_width"] in (64, 96, 128) and t["group"] in (1, 2, 4)
+        else:
+            assert table == []
+    assert np.array_equal(outs[0], outs[1])
