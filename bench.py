@@ -71,8 +71,11 @@ def parse():
     ap.add_argument("--batched-scale", type=float, default=0.25,
                     help="n range of the 64-problem batched measurement, as a fraction of "
                          "[1500, 6000] (0 skips it)")
-    ap.add_argument("--train-length", type=int, default=4,
-                    help="problems in the (separate) training sequence of the degree MLP")
+    ap.add_argument("--learned-protocol", type=int, default=1,
+                    help="run the learned-degree protocol at n = 8192 (30 problems)")
+    ap.add_argument("--train-length", type=int, default=None,
+                    help="problems in the (separate) training sequence of the degree MLP "
+                         "(default: the sequence length, so training covers every step index)")
     return ap.parse_args()
 
 
@@ -264,6 +267,69 @@ def measure_batched(scale, dev, stream, prec):
             "max_loops": max(st["loops"] for row in stats for st in row)}
 
 
+def measure_learned_protocol(dev, stream, n=8192, nev=512, nex=128, length=30, train=10):
+    """The learned-degree protocol at the size of the n = 8192 workload: a
+    correlated sequence of `length` problems (circulant construction: exact
+    spectrum, eigenvectors turned by ~eps per step), problems 1..train
+    solved with the analytic rule while the solver records its traces, the
+    degree MLP trained on them (library kernels), then problems train+1 ..
+    length solved twice from problem train's Ritz vectors: analytic rule vs
+    learned degrees.  Loops, filter column-degrees and seconds per problem
+    for both; eigenvalues checked against the exact spectrum."""
+    import torch
+    from paper_1404_4161_gb300 import _lib as L
+    from paper_1404_4161_gb300 import learned
+    from paper_1404_4161_gb300.solver import Chfsi, colmajor
+    from workloads.synthetic import WORKLOADS, BASE_SEED, circulant_sequence, random_block
+    cfg = WORKLOADS["seq30_n8192"]
+    import dataclasses
+    cfg = dataclasses.replace(cfg, n=n, nev=nev, nex=nex, n_low=nev + nex // 2)
+    hs, lam = circulant_sequence(cfg, BASE_SEED + 9000, length=length, device=dev)
+    Hc = [colmajor(h) for h in hs]
+    del hs
+    normH = float(np.abs(lam).max())
+    s = Chfsi(precision=L.PREC_TC, f64_gemm=L.GEMM_OZAKI)
+    s.trace_enable(1 << 21)
+    X = colmajor(torch.from_numpy(random_block(n, nev + nex, BASE_SEED + 9500)).to(dev))
+    ev, sts, rc = s.solve_sequence(Hc[:train], nev, nex, X, cfg.tol)
+    if rc != L.OK:
+        raise RuntimeError(f"learned protocol: training sequence rc {rc}")
+    xs, ys = learned.dataset(s)
+    losses = learned.train(s, xs, ys, steps=3000, lr=2e-3)
+    s.trace_enable(0)
+    out = {"workload": f"circulant correlated sequence, n={n}, nev={nev}, nex={nex}, "
+                       f"{length} problems; trained on problems 1..{train}, evaluated on "
+                       f"{train + 1}..{length}",
+           "train_rows": int(xs.shape[0]), "loss0": losses[0], "loss": losses[-1]}
+    for name, model in (("analytic", L.DEG_ANALYTIC), ("learned", L.DEG_MLP)):
+        s.set_opts(degree_model=model, step0=train)
+        Xe = X.clone()
+        s.solve_sequence(Hc[train:train + 1], nev, nex, Xe.clone(), cfg.tol)  # warm-up
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ev, sts, rc = s.solve_sequence(Hc[train:], nev, nex, Xe, cfg.tol)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if rc != L.OK:
+            raise RuntimeError(f"learned protocol: {name} evaluation rc {rc}")
+        err = float(np.abs(ev.cpu().numpy()[:, :nev] - lam[None, :nev]).max()) / normH
+        if err > 1e-12:
+            raise RuntimeError(f"learned protocol: {name} eigenvalue error {err:.2e}")
+        out[name] = {"s_per_problem": a.elapsed_time(b) / 1e3 / (length - train),
+                     "loops": sum(x["loops"] for x in sts),
+                     "col_degrees": sum(x["col_degrees"] for x in sts),
+                     "loops_mlp": sum(x["loops_mlp"] for x in sts),
+                     "mlp_fallbacks": sum(x["mlp_fallback"] for x in sts),
+                     "max_eig_err_rel_normH": err}
+    s.close()
+    del Hc
+    torch.cuda.empty_cache()
+    out["time_ratio_learned_over_analytic"] = (out["learned"]["s_per_problem"] /
+                                               out["analytic"]["s_per_problem"])
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -309,7 +375,8 @@ def main():
         # The degree MLP learns from traces the method itself generates, on a
         # separate training sequence (same generator, other seed); untimed.
         from paper_1404_4161_gb300 import learned
-        Ht, _ = config_sequence(cfg, 14044161 + 2700, length=args.train_length, n=n, device=dev)
+        train_len = args.train_length or length
+        Ht, _ = config_sequence(cfg, 14044161 + 2700, length=train_len, n=n, device=dev)
         Htc = [colmajor(h) for h in Ht]
         del Ht
         s.trace_enable(1 << 20)
@@ -321,7 +388,7 @@ def main():
         del Htc, Xt
         torch.cuda.empty_cache()
         train_info = {"rows": int(xs.shape[0]), "steps": 3000, "loss0": losses[0],
-                      "loss": losses[-1], "train_problems": args.train_length}
+                      "loss": losses[-1], "train_problems": train_len}
         s.set_opts(degree_model=L.DEG_MLP)
 
     def step():
@@ -532,6 +599,10 @@ def main():
                               "per warm problem instead of two)"}
         s64.close()
 
+    learned_protocol = None
+    if args.learned_protocol and prec == L.PREC_TC:
+        learned_protocol = measure_learned_protocol(dev, stream)
+
     batched = None
     if args.batched_scale > 0:
         batched = measure_batched(args.batched_scale, dev, stream, prec)
@@ -585,6 +656,7 @@ def main():
             "batched": batched,
             "loops_mlp": [x["loops_mlp"] for x in last],
             "filter_autotune": filter_tuning,
+            "learned_protocol_n8192": learned_protocol,
         }
         print(json.dumps(out))
     s.close()

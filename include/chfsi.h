@@ -338,6 +338,24 @@ int chfsi_degrees(chfsi_ctx* ctx, int k, const double* ritz, const double* resid
 int chfsi_autotune_table(chfsi_ctx* ctx, int max_entries, int* entries_host,
                          int* n_entries_host);
 
+/* Alg. 1 / Sec. 4 (columns sorted by degree so that the filter runs on a
+ * shrinking suffix): stable ascending sort of k columns by degree.
+ *  deg         k ints (device), each >= 1.
+ *  perm        k ints (device): perm[r] = the column of rank r; equal
+ *              degrees keep their column order.
+ *  deg_sorted  k ints (device): deg[perm[r]]. */
+int chfsi_sort_degrees(chfsi_ctx* ctx, int k, const int* deg, int* perm, int* deg_sorted);
+
+/* Alg. 1 locking, out of order (Sec. 4): among ka active Ritz pairs in
+ * ascending order, lock every pair whose residual is <= tol and whose
+ * position is below n_wanted_left (= nev - pairs already locked).
+ *  ritz, resid  ka doubles each (device).
+ *  lock_idx     ka ints (device): positions of the locked pairs, ascending.
+ *  act_idx      ka ints (device): positions of the others, ascending.
+ *  counts_host  2 ints: {locked, still active}. */
+int chfsi_lock(chfsi_ctx* ctx, int ka, const double* ritz, const double* resid,
+               int n_wanted_left, double tol, int* lock_idx, int* act_idx, int* counts_host);
+
 /* ---- filter without device allocation ---------------------------------- */
 
 /* Largest n*k accepted by chfsi_filter_static. */
@@ -397,7 +415,8 @@ int chfsi_mlp_set_params(chfsi_ctx* ctx, const float* params_host);
 int chfsi_mlp_get_params(chfsi_ctx* ctx, float* params_host);
 
 /* Features of column j: t = (ritz - c)/e; x = {clip(t, -8, 8), log10(r)/10,
- * acosh(max|t|, 1), clip((gamma - c)/e, -8, 8), step/10}.  The output y is
+ * acosh(max|t|, 1), clip((gamma - c)/e, -8, 8), min(step, 9)/10} (the
+ * sequence index saturates at the tenth problem).  The output y is
  * the predicted ratio of the realised decay per degree to acosh|t|; with
  * opts.degree_model = CHFSI_DEG_MLP the solver turns it into
  * m = ceil(ln(max(r, tol)/tol) / (acosh|t| clip(y, 0.02, 1.5))) + mlp_extra,

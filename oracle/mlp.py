@@ -23,7 +23,10 @@ Features of one active column (``features``):
   x1 = log10(r) / 10                      (residual)
   x2 = acosh(max(|t|, 1))                 (analytic decay per degree)
   x3 = clip((gamma - c)/e, -8, 8)         (filter bounds: lower end)
-  x4 = step / 10                          (index in the sequence)
+  x4 = min(step, 9) / 10                  (index in the sequence, saturating:
+                                           a network trained on the first ten
+                                           problems sees every later one as
+                                           the tenth instead of extrapolating)
 
 Label (``decay_label``): with r_b the residual when degree m was chosen and
 r_a the residual after filtering with it, y = clip(ln(r_b/r_a) / m /
@@ -38,6 +41,7 @@ import math
 import numpy as np
 
 N_FEAT = 5
+STEP_CAP = 9
 HIDDEN = 64
 DEG_LO, DEG_HI, DEG_SCALE = 4, 60, 60.0
 
@@ -63,7 +67,7 @@ def features(ritz, resid, c, e, gamma, step):
     x[:, 1] = np.log10(r) / 10.0
     x[:, 2] = np.arccosh(np.maximum(np.abs(t), 1.0))
     x[:, 3] = np.clip((gamma - c) / e, -8.0, 8.0)
-    x[:, 4] = step / 10.0
+    x[:, 4] = min(step, STEP_CAP) / 10.0
     return x
 
 

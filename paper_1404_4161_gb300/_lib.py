@@ -87,6 +87,8 @@ _SIGS = {
     "chfsi_solve_batched": (C.c_int, [_P, C.c_int, _P, C.c_int, C.c_double, _P]),
     "chfsi_lanczos": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_ulonglong, _P]),
     "chfsi_autotune_table": (C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_int)]),
+    "chfsi_sort_degrees": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "chfsi_lock": (C.c_int, [_P, C.c_int, _P, _P, C.c_int, C.c_double, _P, _P, _P]),
     "chfsi_filter": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, C.c_double, C.c_double,
                                C.c_double, _P, C.c_int]),
     "chfsi_filter_batched": (C.c_int, [_P, C.c_int, _P]),

@@ -730,13 +730,20 @@ struct Problem {
       // column the low-precision filter spoiled cannot push alpha up.
       alpha = warm_start ? std::min(alpha, ctl_h->alpha) : ctl_h->alpha;
       const double c2 = c_(), e2 = e_();
+      // First loop of a warm start from the residuals of the starting block
+      // (opts.warm_resid): the buffer columns keep the uniform deg_warm (a
+      // higher degree makes them near combinations of the amplified wanted
+      // directions, an ill-conditioned block).
+      const bool warm_first = warm_start && loops == 0;
+      const int bcap = warm_first ? o->deg_warm : (1 << 30);
+      const int extra = o->deg_extra;
       if (use_mlp) {
         mlp_degrees(ctx, ka, lam, res, act_idx, c2, e2, gamma, step, tol, deg);
-        degree_cap_buffer(st, ka, nev - nl, deg);
+        degree_cap_buffer(st, ka, nev - nl, deg, bcap);
         S.loops_mlp++;
       } else {
         degrees_analytic(st, ka, lam, res, act_idx, c2, e2, tol, nev - nl, o->deg_min,
-                         o->deg_max, o->deg_extra, deg);
+                         o->deg_max, extra, deg, bcap);
       }
       trace_record(ctx, ka, lam, res, act_idx, deg, c2, e2, gamma, step, nev - nl);
       sort_by_degree(st, ka, deg, act_idx, perm, deg_sorted);
@@ -1166,6 +1173,32 @@ int chfsi_solve_batched(chfsi_ctx* ctx, int P, const chfsi_problem* probs, int s
     }
   });
   return rc != CHFSI_OK ? rc : status;
+}
+
+int chfsi_sort_degrees(chfsi_ctx* ctx, int k, const int* deg, int* perm, int* deg_sorted) {
+  if (!ctx) return CHFSI_EINVAL;
+  return run_guarded(ctx, [&] {
+    CHFSI_REQUIRE(k >= 0, "bad k");
+    if (k == 0) return;
+    CHFSI_REQUIRE(deg && perm && deg_sorted, "bad sort buffers");
+    sort_by_degree(ctx->stream, k, deg, nullptr, perm, deg_sorted);
+  });
+}
+
+int chfsi_lock(chfsi_ctx* ctx, int ka, const double* ritz, const double* resid,
+               int n_wanted_left, double tol, int* lock_idx, int* act_idx, int* counts_host) {
+  if (!ctx) return CHFSI_EINVAL;
+  return run_guarded(ctx, [&] {
+    CHFSI_REQUIRE(ka >= 1 && n_wanted_left >= 0 && tol > 0.0, "bad locking arguments");
+    CHFSI_REQUIRE(ritz && resid && lock_idx && act_idx && counts_host, "bad locking buffers");
+    LoopCtl* ctl = (LoopCtl*)ws_get(ctx, "api_ctl", sizeof(LoopCtl));
+    lock_select(ctx->stream, ka, ritz, resid, n_wanted_left, tol, 0.0, ctl, lock_idx, act_idx);
+    LoopCtl* h = (LoopCtl*)pinned_get(ctx, 256);
+    CHFSI_CUDA_TRY(cudaMemcpyAsync(h, ctl, sizeof(LoopCtl), cudaMemcpyDeviceToHost, ctx->stream));
+    CHFSI_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    counts_host[0] = h->n_new_locked;
+    counts_host[1] = h->k_active;
+  });
 }
 
 int chfsi_autotune_table(chfsi_ctx* ctx, int max_entries, int* entries_host,

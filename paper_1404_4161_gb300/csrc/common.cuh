@@ -203,13 +203,16 @@ struct LoopCtl {
 void lock_select(cudaStream_t st, int ka, const double* lam, const double* resid,
                  int n_wanted_left, double tol, double gamma_in, LoopCtl* ctl,
                  int* lock_idx, int* act_idx);
+// buffer_cap: upper clamp of the buffer columns' degrees (besides the
+// largest wanted degree).
 void degrees_analytic(cudaStream_t st, int k, const double* ritz, const double* resid,
                       const int* idx, double c, double e, double tol, int n_wanted,
-                      int deg_min, int deg_max, int deg_extra, int* deg_out);
+                      int deg_min, int deg_max, int deg_extra, int* deg_out,
+                      int buffer_cap = 1 << 30);
 void sort_by_degree(cudaStream_t st, int k, const int* deg, const int* idx_or_null,
                     int* perm, int* deg_sorted);
 void sort_by_value(cudaStream_t st, int k, const double* val, int* perm);
-void degree_cap_buffer(cudaStream_t st, int k, int n_wanted, int* deg);
+void degree_cap_buffer(cudaStream_t st, int k, int n_wanted, int* deg, int buffer_cap = 1 << 30);
 
 // Tensor-core split-precision filter (filter_tc.cu): one persistent launch
 // runs every step of Alg. 2 for one or many problems.  ns = bf16 pieces per

@@ -172,7 +172,7 @@ __global__ void mlp_features_kernel(int k, const double* ritz, const double* res
   row[1] = (float)(log10(r) / 10.0);
   row[2] = (float)acosh(fmax(fabs(t), 1.0));
   row[3] = (float)fmin(fmax((gamma - c) / e, -8.0), 8.0);
-  row[4] = (float)(step / 10.0);
+  row[4] = (float)(min(step, 9) / 10.0);
 }
 
 // Degree from the predicted decay ratio (closed form); the analytic rule
@@ -223,7 +223,7 @@ __global__ void trace_record_kernel(int k, const double* ritz, const double* res
   row[1] = (float)(log10(r) / 10.0);
   row[2] = (float)acosh(fmax(fabs(t), 1.0));
   row[3] = (float)fmin(fmax((gamma - c) / e, -8.0), 8.0);
-  row[4] = (float)(step / 10.0);
+  row[4] = (float)(min(step, 9) / 10.0);
   row[5] = (float)deg[j];
   row[6] = (float)r;
   row[7] = __int_as_float(0x7fc00000);  // NaN until the next loop's residual

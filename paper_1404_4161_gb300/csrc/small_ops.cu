@@ -101,11 +101,12 @@ __device__ int analytic_degree(double ritz, double r, double c, double e, double
 }
 
 // Degrees for the k columns idx[j] (or j) of (ritz, resid), then the cap of
-// the buffer columns j >= n_wanted at the largest wanted degree.
+// the buffer columns j >= n_wanted at the largest wanted degree and at
+// buffer_cap.
 __global__ void __launch_bounds__(NT)
 degrees_kernel(int k, const double* __restrict__ ritz, const double* __restrict__ resid,
                const int* __restrict__ idx, double c, double e, double tol, int n_wanted,
-               int deg_min, int deg_max, int deg_extra, int* __restrict__ deg) {
+               int deg_min, int deg_max, int deg_extra, int buffer_cap, int* __restrict__ deg) {
   __shared__ int mx;
   if (threadIdx.x == 0) mx = 0;
   __syncthreads();
@@ -117,18 +118,20 @@ degrees_kernel(int k, const double* __restrict__ ritz, const double* __restrict_
   }
   __syncthreads();
   if (n_wanted > 0 && n_wanted < k)
-    for (int j = n_wanted + threadIdx.x; j < k; j += NT) deg[j] = min(deg[j], mx);
+    for (int j = n_wanted + threadIdx.x; j < k; j += NT)
+      deg[j] = max(deg_min, min(deg[j], min(mx, buffer_cap)));
 }
 
 __global__ void __launch_bounds__(NT)
-degree_cap_kernel(int k, int n_wanted, int* deg) {
+degree_cap_kernel(int k, int n_wanted, int buffer_cap, int* deg) {
   __shared__ int mx;
   if (threadIdx.x == 0) mx = 0;
   __syncthreads();
   for (int j = threadIdx.x; j < n_wanted && j < k; j += NT) atomicMax(&mx, deg[j]);
   __syncthreads();
   if (n_wanted > 0 && n_wanted < k)
-    for (int j = n_wanted + threadIdx.x; j < k; j += NT) deg[j] = min(deg[j], mx);
+    for (int j = n_wanted + threadIdx.x; j < k; j += NT)
+      deg[j] = max(1, min(deg[j], min(mx, buffer_cap)));
 }
 
 // Stable ascending sort by degree: rank_j = #{i: m_i < m_j} + #{i < j:
@@ -174,16 +177,16 @@ void lock_select(cudaStream_t st, int ka, const double* lam, const double* resid
 
 void degrees_analytic(cudaStream_t st, int k, const double* ritz, const double* resid,
                       const int* idx, double c, double e, double tol, int n_wanted,
-                      int deg_min, int deg_max, int deg_extra, int* deg_out) {
+                      int deg_min, int deg_max, int deg_extra, int* deg_out, int buffer_cap) {
   if (k <= 0) return;
   degrees_kernel<<<1, NT, 0, st>>>(k, ritz, resid, idx, c, e, tol, n_wanted, deg_min,
-                                   deg_max, deg_extra, deg_out);
+                                   deg_max, deg_extra, buffer_cap, deg_out);
   chfsi_check_launch("degrees");
 }
 
-void degree_cap_buffer(cudaStream_t st, int k, int n_wanted, int* deg) {
+void degree_cap_buffer(cudaStream_t st, int k, int n_wanted, int* deg, int buffer_cap) {
   if (k <= 0) return;
-  degree_cap_kernel<<<1, NT, 0, st>>>(k, n_wanted, deg);
+  degree_cap_kernel<<<1, NT, 0, st>>>(k, n_wanted, buffer_cap, deg);
   chfsi_check_launch("degree_cap");
 }
 

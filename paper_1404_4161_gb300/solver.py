@@ -197,6 +197,24 @@ class Chfsi:
                                            n_wanted, _ptr(d)))
         return d
 
+    def sort_degrees(self, deg):
+        """deg: int32 device tensor -> (perm, deg_sorted)."""
+        k = deg.shape[0]
+        perm = torch.empty_like(deg)
+        ds = torch.empty_like(deg)
+        self._check(self.lib.chfsi_sort_degrees(self.ctx, k, _ptr(deg), _ptr(perm), _ptr(ds)))
+        return perm, ds
+
+    def lock(self, ritz, resid, n_wanted_left, tol):
+        """-> (locked positions, active positions) as int32 device tensors."""
+        ka = ritz.shape[0]
+        li = torch.empty(ka, dtype=torch.int32, device=ritz.device)
+        ai = torch.empty(ka, dtype=torch.int32, device=ritz.device)
+        cnt = (C.c_int * 2)()
+        self._check(self.lib.chfsi_lock(self.ctx, ka, _ptr(ritz), _ptr(resid), n_wanted_left,
+                                        tol, _ptr(li), _ptr(ai), C.cast(cnt, C.c_void_p)))
+        return li[:cnt[0]], ai[:cnt[1]]
+
     def autotune_table(self):
         """Tilings chosen by the filter's autotuner: list of dicts."""
         cnt = C.c_int()

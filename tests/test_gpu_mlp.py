@@ -94,8 +94,8 @@ def test_learned_degrees_ab():
     rule (a) on random-start solves of problems 11, 20 and 30 and (b) on the
     warm-started continuation 11-30.  Both must reach the tolerance.  The
     learned degrees must save outer loops on the random starts (each loop
-    costs an FP64 Rayleigh-Ritz and QR) and must not cost more than one
-    extra loop over the continuation; the gains are printed."""
+    costs an FP64 Rayleigh-Ritz and QR) and must not add a loop over the
+    continuation; loops and times are printed."""
     from paper_1404_4161_gb300.build import build
     build()
     cfg = WORKLOADS["seq30_n8192"]
@@ -149,5 +149,9 @@ def test_learned_degrees_ab():
     R = np.linalg.norm(H @ X[:, :nev] - X[:, :nev] * e_last[:nev], axis=0) / normH
     assert R.max() <= tol
     assert np.abs(e_last[:nev] - w[:nev]).max() <= 1e-12 * normH
+    # The gain is on random starts (fewer outer loops, each one an FP64
+    # Rayleigh-Ritz and QR); on the warm continuation both converge in the
+    # same number of loops (the analytic rule already lands the residuals
+    # just below tol), so the learned degrees may not add a loop there.
     assert cm < ca
-    assert wm <= wa + 1
+    assert wm <= wa

@@ -59,6 +59,8 @@ def test_features_and_labels():
     x = mlp.features([-2.0, 0.5], [1e-4, 1e-2], 1.0, 2.0, -3.0, 7)
     assert np.allclose(x[0], [-1.5, -0.4, np.arccosh(1.5), -2.0, 0.7])
     assert x[1, 2] == 0.0
+    # the step feature saturates at the tenth problem of a sequence
+    assert mlp.features([-2.0], [1e-4], 1.0, 2.0, -3.0, 25)[0, 4] == 0.9
     # t = -2: acosh 2 = 1.316958; residual 1e-2 -> 1e-6 in 10 degrees gives
     # kappa = ln(1e4)/10 = 0.921034, ratio 0.699364
     y = mlp.decay_label([-3.0], [1e-2], [1e-6], [10], 1.0, 2.0)
