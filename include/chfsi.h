@@ -376,16 +376,20 @@ int chfsi_lock(chfsi_ctx* ctx, int ka, const double* ritz, const double* resid,
  * legacy default stream) and is stream-ordered; the call returns without
  * synchronising.
  *
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  All calls share the one array: calls whose
- * work overlaps on the GPU (different streams, or different host threads)
- * race and give wrong results; serialise them.  The buffers are fully
- * written before they are read, so no earlier contents leak into a result.
+ * The first call in each CUDA context of a device looks up the array's
+ * device address (cudaGetSymbolAddress, with that device current) and keeps
+ * it for that context; after a device reset, or a released and re-created
+ * primary context, the next call looks it up again.  Make the first call on
+ * a device (and the first after a reset) before any stream capture.  All
+ * calls share the one array: calls whose work overlaps on the GPU
+ * (different streams, or different host threads) race and give wrong
+ * results; serialise them.  The buffers are fully written before they are
+ * read, so no earlier contents leak into a result.
  *
  * Returns CHFSI_ETOOBIG when n * k > CHFSI_FILTER_STATIC_MAX_NK (no work is
- * issued), CHFSI_EINVAL for the argument errors of chfsi_filter, CHFSI_ECUDA
- * when the address lookup or a launch fails. */
+ * issued), CHFSI_EINVAL for the argument errors of chfsi_filter and when Y
+ * overlaps Y0 or H in memory, CHFSI_ECUDA when the address lookup or a
+ * launch fails. */
 int chfsi_filter_static(const double* H, int n, int k, const double* Y0,
                         const int* degrees_host, double lam1, double c, double e,
                         double* Y, void* stream);

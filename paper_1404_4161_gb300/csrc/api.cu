@@ -143,52 +143,10 @@ inline const double2* C2(const double* p) { return reinterpret_cast<const double
 // ------------------------------------------------------- FP64 filter ----
 void filter_f64(chfsi_ctx* ctx, const double2* H, int n, int k, const double2* Y0,
                 const int* deg, double lam1, double c, double e, double2* Yout) {
-  cudaStream_t st = ctx->stream;
   const size_t blk = sizeof(double2) * (size_t)n * k;
   double2* F[3] = {(double2*)ws_get(ctx, "flt0", blk), (double2*)ws_get(ctx, "flt1", blk),
                    (double2*)ws_get(ctx, "flt2", blk)};
-  auto buf = [&](int i) -> const double2* { return i == 0 ? Y0 : F[i % 3]; };
-  const int mk = deg[k - 1];
-  const double sigma1 = e / (lam1 - c);
-  int s = (int)(std::upper_bound(deg, deg + k, 1) - deg);
-  {
-    EpiNN ep;
-    ep.alpha = sigma1 / e;
-    ep.shift = c;
-    ep.S = Y0;
-    ep.lds = n;
-    ep.D = F[1];
-    ep.ldd = n;
-    ep.F = Yout;
-    ep.ldf = n;
-    ep.fin_end = s;
-    zgemm_nn(st, n, k, n, H, n, Y0, n, ep);
-  }
-  double sigma = sigma1;
-  for (int i = 1; i < mk; ++i) {
-    const double sn = 1.0 / (2.0 / sigma1 - sigma);
-    const int s_new = (int)(std::upper_bound(deg, deg + k, i + 1) - deg);
-    const double2* cur = buf(i);
-    const double2* prev = buf(i - 1);
-    double2* nxt = F[(i + 1) % 3];
-    const size_t off = (size_t)s * n;
-    EpiNN ep;
-    ep.alpha = 2.0 * sn / e;
-    ep.shift = c;
-    ep.S = cur + off;
-    ep.lds = n;
-    ep.beta = -sn * sigma;
-    ep.P = prev + off;
-    ep.ldp = n;
-    ep.D = nxt + off;
-    ep.ldd = n;
-    ep.F = Yout + off;
-    ep.ldf = n;
-    ep.fin_end = s_new - s;
-    zgemm_nn(st, n, k - s, n, H, n, cur + off, n, ep);
-    sigma = sn;
-    s = s_new;
-  }
+  filter_f64_recurrence(ctx->stream, H, n, k, Y0, deg, lam1, c, e, Yout, F);
 }
 
 // ------------------------------------------------- cuSOLVER helpers ----

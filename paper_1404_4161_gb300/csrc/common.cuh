@@ -142,6 +142,12 @@ struct EpiNN {
 void zgemm_nn(cudaStream_t st, int M, int N, int K, const double2* A, int lda,
               const double2* B, int ldb, const EpiNN& ep);
 
+// Alg. 2 in FP64 on the k degree-sorted columns of Y0 (deg ascending, host)
+// into Yout; F: three caller-owned n x k work buffers.
+void filter_f64_recurrence(cudaStream_t st, const double2* H, int n, int k, const double2* Y0,
+                           const int* deg, double lam1, double c, double e, double2* Yout,
+                           double2* const F[3]);
+
 // C (K1 x K2, ldc) = alpha * A^H B + beta * C, A: Nr x K1, B: Nr x K2 (split
 // over the long dimension Nr, partial sums reduced in a fixed order).
 void zgemm_cn(chfsi_ctx* ctx, int K1, int K2, int Nr, const double2* A, int lda,

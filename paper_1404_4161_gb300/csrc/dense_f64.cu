@@ -9,6 +9,8 @@
 // so these kernels are bound by DFMA issue at any practical size: a 32 x 32
 // complex output tile per 256-thread CTA with a 2 x 2 register tile keeps
 // the pipe fed, and grids are sized to cover all 152 SMs several times.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace {
@@ -563,4 +565,57 @@ void ns_matrix(cudaStream_t st, int k, const double2* G, double2* T) {
   ns_matrix_kernel<<<(unsigned)std::min<size_t>(((size_t)k * k + 255) / 256, 1024), 256, 0, st>>>(
       k, G, T);
   chfsi_check_launch("ns_matrix");
+}
+
+// Alg. 2 in FP64 (readings R1, R2 of the column ranges): Y_1 = sigma_1/e
+// (H - cI) Y_0 on all k columns, then for i = 1 .. m_k - 1 the step
+// Y_{i+1} = 2 sigma_{i+1}/e (H - cI) Y_i - sigma_{i+1} sigma_i Y_{i-1} on the
+// columns whose degree exceeds i; a column's result goes to Yout at the step
+// that reaches its degree.  deg (host) ascending; F: three n x k work
+// buffers (caller-owned, fully written before they are read).
+void filter_f64_recurrence(cudaStream_t st, const double2* H, int n, int k, const double2* Y0,
+                           const int* deg, double lam1, double c, double e, double2* Yout,
+                           double2* const F[3]) {
+  auto buf = [&](int i) -> const double2* { return i == 0 ? Y0 : F[i % 3]; };
+  const int mk = deg[k - 1];
+  const double sigma1 = e / (lam1 - c);
+  int s = (int)(std::upper_bound(deg, deg + k, 1) - deg);
+  {
+    EpiNN ep;
+    ep.alpha = sigma1 / e;
+    ep.shift = c;
+    ep.S = Y0;
+    ep.lds = n;
+    ep.D = F[1];
+    ep.ldd = n;
+    ep.F = Yout;
+    ep.ldf = n;
+    ep.fin_end = s;
+    zgemm_nn(st, n, k, n, H, n, Y0, n, ep);
+  }
+  double sigma = sigma1;
+  for (int i = 1; i < mk; ++i) {
+    const double sn = 1.0 / (2.0 / sigma1 - sigma);
+    const int s_new = (int)(std::upper_bound(deg, deg + k, i + 1) - deg);
+    const double2* cur = buf(i);
+    const double2* prev = buf(i - 1);
+    double2* nxt = F[(i + 1) % 3];
+    const size_t off = (size_t)s * n;
+    EpiNN ep;
+    ep.alpha = 2.0 * sn / e;
+    ep.shift = c;
+    ep.S = cur + off;
+    ep.lds = n;
+    ep.beta = -sn * sigma;
+    ep.P = prev + off;
+    ep.ldp = n;
+    ep.D = nxt + off;
+    ep.ldd = n;
+    ep.F = Yout + off;
+    ep.ldf = n;
+    ep.fin_end = s_new - s;
+    zgemm_nn(st, n, k - s, n, H, n, cur + off, n, ep);
+    sigma = sn;
+    s = s_new;
+  }
 }
