@@ -71,6 +71,9 @@ def parse():
     ap.add_argument("--batched-scale", type=float, default=0.25,
                     help="n range of the 64-problem batched measurement, as a fraction of "
                          "[1500, 6000] (0 skips it)")
+    ap.add_argument("--batched-full", type=int, default=0,
+                    help="also run the 64-sequence workload at its stated size (n 1500-6000, "
+                         "10 steps; several minutes)")
     ap.add_argument("--learned-protocol", type=int, default=1,
                     help="run the learned-degree protocol at n = 8192 (30 problems)")
     ap.add_argument("--train-length", type=int, default=None,
@@ -246,7 +249,7 @@ def measure_batched(scale, dev, stream, prec):
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    evs, stats, rc = s.solve_batched(work, 1e-10)
+    evs, stats, rc, _ = s.solve_batched(work, 1e-10)
     b.record(stream)
     torch.cuda.synchronize()
     t_batch = a.elapsed_time(b) / 1e3
@@ -327,6 +330,115 @@ def measure_learned_protocol(dev, stream, n=8192, nev=512, nex=128, length=30, t
     torch.cuda.empty_cache()
     out["time_ratio_learned_over_analytic"] = (out["learned"]["s_per_problem"] /
                                                out["analytic"]["s_per_problem"])
+    return out
+
+
+def measure_batched_full(dev, stream, problems=64, steps=10, window=2, oracle_sample=2):
+    """The k-point-style workload at its stated size: `problems` independent
+    correlated sequences (circulant construction, see
+    workloads.synthetic.circulant_window), n uniform in [1500, 6000]
+    (seeded), nev = n/16, nex = nev/4, `steps` steps each, tol 1e-10.  The
+    steps run in windows of `window` (the matrices of one window are made
+    on the device, untimed; the next window starts warm from the last Ritz
+    blocks).  Timed: the lockstep batched solve (one batched filter launch
+    per outer loop) and the same problems solved one at a time.  Checked:
+    every status, the eigenvalues of every problem and step against the
+    exact spectrum, residuals of the last step.  The oracle (host cores)
+    solves the first two steps of the `oracle_sample` smallest problems."""
+    import torch
+    from paper_1404_4161_gb300 import _lib as L
+    from paper_1404_4161_gb300.solver import Chfsi
+    from workloads.synthetic import WORKLOADS, BASE_SEED, circulant_window, random_block
+    cfg = WORKLOADS["batched64"]
+    rng = np.random.Generator(np.random.PCG64(BASE_SEED + 4000))
+    ns = [int(x) for x in rng.integers(1500, 6001, problems)]
+    dims = [(n, n // 16, (n // 16) // 4) for n in ns]
+    seeds = [BASE_SEED + 4100 + p for p in range(problems)]
+    X0 = [random_block(n, nev + nex, BASE_SEED + 4300 + p) for p, (n, nev, nex) in enumerate(dims)]
+    out = {"workload": f"{problems} correlated sequences (circulant), n uniform in [1500, 6000] "
+                       f"(min {min(ns)}, max {max(ns)}), nev = n/16, nex = nev/4, {steps} steps, "
+                       f"tol 1e-10, windows of {window} steps",
+           "problem_steps": problems * steps}
+    for mode in ("batched", "one_at_a_time"):
+        s = Chfsi(precision=L.PREC_TC, f64_gemm=L.GEMM_OZAKI, profile=1)
+        Xs = [torch.from_numpy(x).to(dev).t().contiguous() for x in X0]
+        warm = None
+        t_solve, loops, filt_ms, filt_fl, eig_err, resid = 0.0, 0, 0.0, 0.0, 0.0, 0.0
+        for w0 in range(0, steps, window):
+            cnt = min(window, steps - w0)
+            hs, lams = [], []
+            for p, (n, nev, nex) in enumerate(dims):
+                h, lam = circulant_window(cfg, seeds[p], w0, cnt, n, device=dev)
+                hs.append([x.t().contiguous() for x in h])
+                lams.append(lam)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            if mode == "batched":
+                seqs = [(hs[p], nev, nex, Xs[p]) for p, (n, nev, nex) in enumerate(dims)]
+                evs, stats, rc, warm = s.solve_batched(seqs, cfg.tol, warm=warm)
+                if rc != L.OK:
+                    raise RuntimeError(f"batched64: rc {rc} at steps {w0}..{w0 + cnt - 1}")
+                flat = [st for row in stats for st in row]
+                filt_ms += sum(row[0]["k_tc_ms"] for row in stats)
+                filt_fl += sum(row[0]["k_tc_flops"] for row in stats)
+                evs = [e.cpu().numpy() for e in evs]
+            else:
+                warm = warm or [None] * problems
+                evs, flat = [], []
+                for p, (n, nev, nex) in enumerate(dims):
+                    rows = []
+                    for l in range(cnt):
+                        s.set_opts(step0=w0 + l)
+                        ev, st, rc = s.solve(hs[p][l], nev, nex, Xs[p], cfg.tol, warm=warm[p])
+                        if rc != L.OK:
+                            raise RuntimeError(f"batched64 one-at-a-time: rc {rc}")
+                        warm[p] = (float(ev[0]), float(ev[-1]))
+                        rows.append(ev.cpu().numpy())
+                        flat.append(st)
+                    evs.append(np.vstack(rows))
+            b.record(stream)
+            torch.cuda.synchronize()
+            t_solve += a.elapsed_time(b) / 1e3
+            loops += sum(st["loops"] for st in flat)
+            for p, (n, nev, nex) in enumerate(dims):
+                normH = float(np.abs(lams[p]).max())
+                eig_err = max(eig_err, float(np.abs(evs[p][:, :nev] - lams[p][None, :nev]).max())
+                              / normH)
+                if w0 + cnt == steps:
+                    H = hs[p][-1].t()
+                    X = Xs[p].t()[:, :nev]
+                    ev_last = torch.from_numpy(evs[p][-1, :nev]).to(dev)
+                    R = torch.linalg.vector_norm(H @ X - X * ev_last.to(X.dtype), dim=0)
+                    resid = max(resid, float(R.max()) / normH)
+            del hs
+            torch.cuda.empty_cache()
+        s.close()
+        if eig_err > 1e-12 or resid > cfg.tol:
+            raise RuntimeError(f"batched64 {mode}: eigenvalue error {eig_err:.2e}, "
+                               f"residual {resid:.2e}")
+        out[mode] = {"s_per_problem": t_solve / (problems * steps), "loops": loops,
+                     "max_eig_err_rel_normH": eig_err, "max_resid_last_step": resid}
+        if mode == "batched" and filt_ms > 0:
+            out[mode]["filter_useful_tflops"] = filt_fl / (filt_ms / 1e3) / 1e12
+    if oracle_sample:
+        import oracle
+        order = np.argsort(ns)[:oracle_sample]
+        t, cnt = 0.0, 0
+        for p in order:
+            n, nev, nex = dims[p]
+            hs, lam = circulant_window(cfg, seeds[p], 0, 2, n)
+            X, wv = X0[p], None
+            for h in hs:
+                t0 = time.perf_counter()
+                r = oracle.chfsi(h.numpy(), nev, nex, X, cfg.tol, warm=wv)
+                t += time.perf_counter() - t0
+                cnt += 1
+                X, wv = r["X"], (r["evals"][0], r["evals"][-1])
+        out["cpu_oracle"] = {"s_per_problem": t / cnt, "cores": os.cpu_count(),
+                             "sample": f"steps 1-2 of the {oracle_sample} smallest problems "
+                                       f"(n = {[ns[p] for p in order]})"}
     return out
 
 
@@ -606,6 +718,9 @@ def main():
     batched = None
     if args.batched_scale > 0:
         batched = measure_batched(args.batched_scale, dev, stream, prec)
+    batched_full = None
+    if args.batched_full and prec == L.PREC_TC:
+        batched_full = measure_batched_full(dev, stream)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -654,6 +769,7 @@ def main():
             "analytic_degrees_gpu": analytic_cmp,
             "mlp_training": train_info,
             "batched": batched,
+            "batched64_full": batched_full,
             "loops_mlp": [x["loops_mlp"] for x in last],
             "filter_autotune": filter_tuning,
             "learned_protocol_n8192": learned_protocol,

@@ -223,17 +223,24 @@ typedef struct chfsi_problem {
   double* X;                   /* device, complex n x (nev+nex): in X0,     */
                                /* out the Ritz block of the last step        */
   double* evals;               /* device, steps x (nev+nex) doubles          */
+  int warm;                    /* in: 1 = X holds the Ritz vectors of an     */
+                               /* earlier step of this sequence and          */
+                               /* lam_lo, lam_hi its lambda_1, lambda_k (the */
+                               /* first step starts warm); 0 = random X0     */
+  double lam_lo, lam_hi;       /* in (warm = 1) / out: lambda_1, lambda_k of */
+                               /* the last step solved                       */
 } chfsi_problem;
 
 /* Many independent sequences (k-point style) solved in lockstep: at each
- * step l, problem p starts from its step l-1 Ritz block (random start at
- * l = 0), and every outer loop filters all unconverged problems in ONE
+ * step l, problem p starts from its step l-1 Ritz block (at l = 0 from X
+ * as the problem's warm field says), and every outer loop filters all
+ * unconverged problems in ONE
  * batched persistent tensor-core launch (opts.precision CHFSI_PREC_TC or
  * CHFSI_PREC_MIXED; FP64 filters run per problem), followed by each
  * problem's QR, Rayleigh-Ritz, residuals, locking and degrees.
  *  stats_host  NULL or steps * P structs, entry l * P + p; with
  *  opts.profile the batch's kernel times are reported in entry l * P. */
-int chfsi_solve_batched(chfsi_ctx* ctx, int P, const chfsi_problem* probs, int steps,
+int chfsi_solve_batched(chfsi_ctx* ctx, int P, chfsi_problem* probs, int steps,
                         double tol, chfsi_stats* stats_host);
 
 /* ---- the steps of the hot path, one entry point each ------------------ */

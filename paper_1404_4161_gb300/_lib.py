@@ -59,7 +59,8 @@ class FilterItem(C.Structure):
 
 class Problem(C.Structure):
     _fields_ = [("H_host", C.c_void_p), ("n", C.c_int), ("nev", C.c_int), ("nex", C.c_int),
-                ("X", C.c_void_p), ("evals", C.c_void_p)]
+                ("X", C.c_void_p), ("evals", C.c_void_p), ("warm", C.c_int),
+                ("lam_lo", C.c_double), ("lam_hi", C.c_double)]
 
 
 class ChfsiError(RuntimeError):

@@ -1089,7 +1089,7 @@ int chfsi_solve_sequence_host(chfsi_ctx* ctx, const double* const* H, int N, int
   return rc != CHFSI_OK ? rc : status;
 }
 
-int chfsi_solve_batched(chfsi_ctx* ctx, int P, const chfsi_problem* probs, int steps,
+int chfsi_solve_batched(chfsi_ctx* ctx, int P, chfsi_problem* probs, int steps,
                         double tol, chfsi_stats* stats) {
   if (!ctx) return CHFSI_EINVAL;
   int status = CHFSI_OK;
@@ -1100,13 +1100,20 @@ int chfsi_solve_batched(chfsi_ctx* ctx, int P, const chfsi_problem* probs, int s
     std::vector<double2*> X(P);
     std::vector<double*> ev(P);
     std::vector<double> warm(2 * (size_t)P);
+    bool any_warm = false, all_warm = true;
     for (int p = 0; p < P; ++p) {
       CHFSI_REQUIRE(probs[p].H_host && probs[p].X && probs[p].evals, "NULL in a problem");
+      CHFSI_REQUIRE(probs[p].warm == 0 || probs[p].warm == 1, "bad warm flag");
       n[p] = probs[p].n;
       nev[p] = probs[p].nev;
       nex[p] = probs[p].nex;
       X[p] = C2(probs[p].X);
+      warm[2 * p] = probs[p].lam_lo;
+      warm[2 * p + 1] = probs[p].lam_hi;
+      any_warm = any_warm || probs[p].warm;
+      all_warm = all_warm && probs[p].warm;
     }
+    CHFSI_REQUIRE(any_warm == all_warm, "the problems of a batch start all warm or all cold");
     for (int l = 0; l < steps; ++l) {
       for (int p = 0; p < P; ++p) {
         H[p] = C2(probs[p].H_host[l]);
@@ -1114,7 +1121,7 @@ int chfsi_solve_batched(chfsi_ctx* ctx, int P, const chfsi_problem* probs, int s
         ev[p] = probs[p].evals + (size_t)l * (nev[p] + nex[p]);
       }
       const int s = solve_batch(ctx, P, H.data(), n.data(), nev.data(), nex.data(), X.data(),
-                                tol, ev.data(), l ? warm.data() : nullptr,
+                                tol, ev.data(), (l || all_warm) ? warm.data() : nullptr,
                                 stats ? stats + (size_t)l * P : nullptr, ctx->opts.step0 + l,
                                 nullptr);
       if (s != CHFSI_OK && status == CHFSI_OK) status = s;
@@ -1128,6 +1135,10 @@ int chfsi_solve_batched(chfsi_ctx* ctx, int P, const chfsi_problem* probs, int s
       }
       CHFSI_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
       std::copy(wh, wh + 2 * P, warm.begin());
+    }
+    for (int p = 0; p < P; ++p) {
+      probs[p].lam_lo = warm[2 * p];
+      probs[p].lam_hi = warm[2 * p + 1];
     }
   });
   return rc != CHFSI_OK ? rc : status;

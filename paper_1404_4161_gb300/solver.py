@@ -97,10 +97,12 @@ class Chfsi:
         self._check(rc, allow)
         return ev, [s.as_dict() for s in st], rc
 
-    def solve_batched(self, seqs, tol, allow=(L.ENOCONV,)):
+    def solve_batched(self, seqs, tol, allow=(L.ENOCONV,), warm=None):
         """seqs: list of (list of Hc per step, nev, nex, Xc); all sequences
-        have the same number of steps.  Returns (evals per problem, stats
-        [step][problem], rc)."""
+        have the same number of steps.  warm: None (random starts) or one
+        (lam_1, lam_k) pair per sequence of the step that produced Xc.
+        Returns (evals per problem, stats [step][problem], rc, warm pairs of
+        the last step)."""
         P = len(seqs)
         steps = len(seqs[0][0])
         probs = (L.Problem * P)()
@@ -110,14 +112,17 @@ class Chfsi:
             keep.append(ptrs)
             ev = torch.empty((steps, nev + nex), dtype=torch.float64, device=Xc.device)
             evs.append(ev)
+            w = warm[p] if warm is not None else (0.0, 0.0)
             probs[p] = L.Problem(C.cast(ptrs, C.c_void_p), Hcs[0].shape[0], nev, nex,
-                                 Xc.data_ptr(), ev.data_ptr())
+                                 Xc.data_ptr(), ev.data_ptr(), 1 if warm is not None else 0,
+                                 float(w[0]), float(w[1]))
         st = (Stats * (P * steps))()
         rc = self.lib.chfsi_solve_batched(self.ctx, P, C.cast(probs, C.c_void_p), steps, tol,
                                           C.cast(st, C.c_void_p))
         self._check(rc, allow)
         stats = [[st[l * P + p].as_dict() for p in range(P)] for l in range(steps)]
-        return evs, stats, rc
+        last = [(probs[p].lam_lo, probs[p].lam_hi) for p in range(P)]
+        return evs, stats, rc, last
 
     # -- single steps -------------------------------------------------
     def lanczos(self, Hc, steps, seed):

@@ -10,7 +10,7 @@ import pytest
 import oracle
 from paper_1404_4161_gb300 import _lib as L
 from paper_1404_4161_gb300.solver import Chfsi
-from tests.gpu_util import colrel, from_dev_cm, known_problem, to_dev_cm
+from tests.gpu_util import DEV, colrel, from_dev_cm, known_problem, to_dev_cm
 from workloads.synthetic import random_block
 
 pytestmark = pytest.mark.gpu
@@ -92,7 +92,7 @@ def test_solve_batched_sequences():
         seqs.append(([to_dev_cm(h) for h in Hs], nev, nex, to_dev_cm(X0)))
         ref.append((Hs, lam, nev))
     s = Chfsi(precision=L.PREC_TC)
-    evs, stats, rc = s.solve_batched(seqs, 1e-10)
+    evs, stats, rc, _ = s.solve_batched(seqs, 1e-10)
     s.close()
     assert rc == L.OK
     for (Hcs, nev, nex, Xc), ev, (Hs, lam, nev_) in zip(seqs, evs, ref):
@@ -106,3 +106,42 @@ def test_solve_batched_sequences():
     for l in range(2):
         for st in stats[l]:
             assert st["status"] == L.OK and st["loops_lowp"] == st["loops"]
+
+
+def test_solve_batched_in_windows_equals_one_call():
+    """Three steps of four sequences solved in one call, or as one step and
+    then two more that start warm from the first call's Ritz blocks and
+    lambda_1, lambda_k (the problems' warm fields): the same eigenvalues,
+    bit for bit."""
+    from paper_1404_4161_gb300.build import build
+    from workloads.synthetic import BASE_SEED, WORKLOADS, circulant_window
+    build()
+    cfg = WORKLOADS["batched64"]
+    sizes = [640, 768, 512, 896]
+    runs = {}
+    for mode in ("one", "windows"):
+        s = Chfsi(precision=L.PREC_TC)
+        seqs, Xs = [], []
+        hs_all = []
+        for i, n in enumerate(sizes):
+            hs, lam = circulant_window(cfg, BASE_SEED + 6000 + i, 0, 3, n, device=DEV)
+            hs_all.append([h.t().contiguous() for h in hs])
+            nev = n // 16
+            nex = nev // 4
+            Xs.append(to_dev_cm(random_block(n, nev + nex, BASE_SEED + 6100 + i)))
+        if mode == "one":
+            seqs = [(hs_all[i], n // 16, (n // 16) // 4, Xs[i]) for i, n in enumerate(sizes)]
+            evs, _, rc, _ = s.solve_batched(seqs, 1e-10)
+            assert rc == L.OK
+            runs[mode] = [e.cpu().numpy() for e in evs]
+        else:
+            seqs = [(hs_all[i][:1], n // 16, (n // 16) // 4, Xs[i]) for i, n in enumerate(sizes)]
+            ev1, _, rc, warm = s.solve_batched(seqs, 1e-10)
+            assert rc == L.OK
+            seqs = [(hs_all[i][1:], n // 16, (n // 16) // 4, Xs[i]) for i, n in enumerate(sizes)]
+            ev2, _, rc, _ = s.solve_batched(seqs, 1e-10, warm=warm)
+            assert rc == L.OK
+            runs[mode] = [np.vstack([a.cpu().numpy(), b.cpu().numpy()]) for a, b in zip(ev1, ev2)]
+        s.close()
+    for a, b in zip(runs["one"], runs["windows"]):
+        assert np.array_equal(a, b)

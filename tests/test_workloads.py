@@ -34,3 +34,21 @@ def test_config_sequence_keeps_spectrum_without_diagonal_term():
     hs, lam = config_sequence(cfg, 5, length=2, n=128, delta=0.0)
     for H in hs:
         assert np.abs(np.linalg.eigvalsh(H) - lam).max() <= 1e-12 * np.abs(lam).max()
+
+
+def test_circulant_window_has_the_spectrum_and_matches_its_windows():
+    """A window of the direct circulant sequence is Hermitian with exactly the
+    workload's spectrum, and problem l is the same whichever window holds it."""
+    import torch
+    from workloads.synthetic import WORKLOADS, circulant_window
+    cfg = WORKLOADS["batched64"]
+    hs, lam = circulant_window(cfg, 77, 0, 3, 96)
+    hs2, lam2 = circulant_window(cfg, 77, 2, 1, 96)
+    assert np.array_equal(lam, lam2)
+    assert torch.equal(hs[2], hs2[0])
+    for h in hs:
+        a = h.numpy()
+        assert np.abs(a - a.conj().T).max() == 0.0
+        assert np.abs(np.linalg.eigvalsh(a) - lam).max() < 1e-12 * np.abs(lam).max()
+    nev = 96 // 16
+    assert (lam < 0).sum() == nev + max(1, nev // 4) // 2

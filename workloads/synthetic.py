@@ -221,3 +221,43 @@ def circulant_sequence(cfg: Config, seed: int, length: int = 2, eps: float | Non
         h = e.unsqueeze(1) * hs[-1] * e.conj().unsqueeze(0)
         hs.append(0.5 * (h + h.conj().T))
     return hs, lam
+
+
+def circulant_window(cfg: Config, seed: int, first: int, count: int, n: int, device=None,
+                     eps: float | None = None):
+    """Problems first .. first + count - 1 of a correlated circulant
+    sequence of size n, made directly (each step is one elementwise pass,
+    so a window of a long sequence costs no more than the window):
+
+    H_l = Phi_l C Phi_l^H, Hermitianised, with C the Hermitian circulant of
+    the workload's spectrum (two bands; n_low = nev + nex/2 with nev = n/16,
+    nex = nev/4 for the per-problem-size workloads) and Phi_l =
+    diag(phi_0 prod_{i<=l} exp(i eps theta_i)), theta_i ~ N(0, 1): every H_l
+    has the spectrum lam exactly, eigenvectors turned by ~eps per step.
+    Returns (list of H as torch complex128 tensors on ``device``, lam)."""
+    import torch
+    eps = cfg.eps if eps is None else eps
+    rng = _rng(seed)
+    if cfg.n == 0:
+        nev = max(1, n // 16)
+        n_low = nev + max(1, nev // 4) // 2
+    else:
+        n_low = cfg.n_low if n == cfg.n else max(1, int(round(cfg.n_low * n / cfg.n)))
+    lam = two_band_spectrum(n, n_low, cfg.low, cfg.bulk, rng)
+    perm = rng.permutation(n)
+    col = np.fft.ifft(lam[perm])
+    phi = np.exp(2j * np.pi * rng.uniform(size=n))
+    col_t = torch.from_numpy(col).to(device)
+    idx = (torch.arange(n, device=device).unsqueeze(1) - torch.arange(n, device=device).unsqueeze(0)) % n
+    c = col_t[idx]
+    del idx
+    out = []
+    for l in range(first + count):
+        if l > 0:
+            phi = phi * np.exp(1j * eps * rng.standard_normal(n))
+        if l >= first:
+            d = torch.from_numpy(phi).to(device)
+            h = d.unsqueeze(1) * c * d.conj().unsqueeze(0)
+            out.append(0.5 * (h + h.conj().T))
+    del c
+    return out, lam
