@@ -30,6 +30,7 @@ from .chfsi import (  # noqa: F401
     cold_interval,
     chfsi,
     chfsi_sequence,
+    chfsi_generalized,
 )
 from .jacobi import jacobi_eigh  # noqa: F401
 from . import mlp  # noqa: F401

@@ -342,3 +342,23 @@ def chfsi_sequence(Hs, nev: int, nex: int, X0, tol: float, **kw) -> list:
         X = res["X"]
         warm = (res["evals"][0], res["evals"][-1])
     return out
+
+
+# ----------------------------------------------------------------------
+# Sec. 3 (the problem statement before Alg. 1): generalized problems
+# ----------------------------------------------------------------------
+def chfsi_generalized(A, B, nev: int, nex: int, X0, tol: float, **kw) -> dict:
+    """A c = lambda B c with A Hermitian and B Hermitian positive definite:
+    the input of Alg. 1 is the reduction to standard form H = L^-1 A L^-H,
+    B = L L^H (Cholesky), whose eigenvectors Y give c = L^-H Y.  X0 is a
+    starting block of H (in a sequence, the previous problem's Y).
+    Returns chfsi's dict plus "C" = L^-H X (B-orthonormal)."""
+    import scipy.linalg as sla
+    L = np.linalg.cholesky(np.asarray(B, dtype=np.complex128))
+    T = sla.solve_triangular(L, np.asarray(A, dtype=np.complex128), lower=True)  # L^-1 A
+    H = sla.solve_triangular(L, T.conj().T, lower=True).conj().T                  # T L^-H
+    H = 0.5 * (H + H.conj().T)
+    res = chfsi(H, nev, nex, X0, tol, **kw)
+    res["C"] = sla.solve_triangular(L.conj().T, res["X"], lower=False)            # L^-H Y
+    res["H"] = H
+    return res

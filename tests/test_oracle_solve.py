@@ -92,3 +92,43 @@ def test_bad_sizes():
         oracle.chfsi(H, 4, 0, random_block(10, 4, 1), 1e-10)
     with pytest.raises(ValueError):
         oracle.chfsi(H, 8, 4, random_block(10, 12, 1), 1e-10)
+
+
+def generalized_known(n, seed, lo=(-2.0, -1.0), bulk=(0.0, 10.0), n_low=None):
+    """A = L V diag(lam) V^H L^H with B = L L^H Hermitian positive definite
+    (eigenvalues in [0.5, 3]) and V Haar unitary: A c = lam B c has exactly
+    the eigenvalues lam, eigenvectors C = L^-H V."""
+    from workloads.synthetic import haar_unitary
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n_low = n_low or max(1, n // 8)
+    lam = np.sort(np.concatenate([rng.uniform(*lo, n_low), rng.uniform(*bulk, n - n_low)]))
+    qb = haar_unitary(n, rng)
+    B = (qb * rng.uniform(0.5, 3.0, n)[None, :]) @ qb.conj().T
+    B = 0.5 * (B + B.conj().T)
+    L = np.linalg.cholesky(B)
+    V = haar_unitary(n, rng)
+    A = L @ ((V * lam[None, :]) @ V.conj().T) @ L.conj().T
+    A = 0.5 * (A + A.conj().T)
+    return A, B, lam
+
+
+def test_generalized_known_spectrum_and_lapack():
+    """Sec. 3: the reduction to standard form, ChFSI, the back-transform.
+    Pinned against the exact generalized spectrum and LAPACK's zhegvd
+    (scipy.linalg.eigh(A, B)); the eigenvectors are B-orthonormal and
+    satisfy A c = lam B c."""
+    import scipy.linalg as sla
+    from workloads.synthetic import random_block
+    n, nev, nex = 160, 12, 6
+    A, B, lam = generalized_known(n, 31)
+    res = oracle.chfsi_generalized(A, B, nev, nex, random_block(n, nev + nex, 32), 1e-10)
+    assert res["status"] == "OK"
+    ev = res["evals"][:nev]
+    w = sla.eigh(A, B, eigvals_only=True)
+    scale = np.abs(lam).max()
+    assert np.abs(ev - lam[:nev]).max() <= 1e-12 * scale
+    assert np.abs(ev - w[:nev]).max() <= 1e-12 * scale
+    C = res["C"][:, :nev]
+    assert np.abs(C.conj().T @ B @ C - np.eye(nev)).max() < 1e-12
+    R = np.linalg.norm(A @ C - (B @ C) * ev[None, :], axis=0)
+    assert R.max() <= 1e-10 * (np.linalg.norm(A, 2) + scale * np.linalg.norm(B, 2))
