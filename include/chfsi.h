@@ -243,6 +243,26 @@ typedef struct chfsi_problem {
 int chfsi_solve_batched(chfsi_ctx* ctx, int P, chfsi_problem* probs, int steps,
                         double tol, chfsi_stats* stats_host);
 
+/* Generalized problem A c = lambda B c (A Hermitian, B Hermitian positive
+ * definite; the form the paper's FLAPW sequences come in, Sec. 3): the
+ * input of Alg. 1 is the reduction to standard form H = L^-1 A L^-H with
+ * B = L L^H (Cholesky), and c = L^-H y.  Here B = R^H R with R = L^H; the
+ * inverse factor W = R^-1 = L^-H comes from the library's inverse-Cholesky
+ * kernel (FP64), H = W^H A W and C = W Y from the context's FP64 product
+ * engine.
+ *  A, B   complex n x n (device), read only.
+ *  X      in: starting block of H (a random block, or in a sequence the
+ *         previous problem's Y, as in the paper); out: Y, the Ritz vectors
+ *         of H (as chfsi_solve).
+ *  C      complex n x (nev+nex) (device) out: W Y, the generalized
+ *         eigenvectors (C^H B C = I).
+ *  evals, warm_host, stats_host as chfsi_solve.
+ *  EBREAKDOWN when B is not numerically positive definite.  The context
+ *  keeps three n x n workspaces for the reduction. */
+int chfsi_solve_generalized(chfsi_ctx* ctx, const double* A, const double* B, int n, int nev,
+                            int nex, double* X, double* C, double tol, double* evals,
+                            const double* warm_host, chfsi_stats* stats_host);
+
 /* ---- the steps of the hot path, one entry point each ------------------ */
 
 /* Alg. 1 (spectral bounds): s-step Lanczos with full reorthogonalisation from the

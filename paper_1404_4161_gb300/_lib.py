@@ -81,6 +81,8 @@ _SIGS = {
     "chfsi_last_error": (C.c_char_p, [_P]),
     "chfsi_solve": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, _P, C.c_double, _P, _P,
                               C.POINTER(Stats)]),
+    "chfsi_solve_generalized": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_int, _P, _P,
+                                          C.c_double, _P, _P, C.POINTER(Stats)]),
     "chfsi_solve_sequence": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, _P,
                                        C.c_double, _P, _P]),
     "chfsi_solve_sequence_host": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, _P,

@@ -1018,6 +1018,45 @@ int chfsi_solve(chfsi_ctx* ctx, const double* H, int n, int nev, int nex, double
   return status;
 }
 
+int chfsi_solve_generalized(chfsi_ctx* ctx, const double* A, const double* B, int n, int nev,
+                            int nex, double* X, double* C, double tol, double* evals,
+                            const double* warm_host, chfsi_stats* stats) {
+  if (!ctx) return CHFSI_EINVAL;
+  int status = CHFSI_OK;
+  int rc = run_guarded(ctx, [&] {
+    CHFSI_REQUIRE(n >= 1 && nev >= 1 && nex >= 1 && nev + nex <= n, "bad generalized sizes");
+    CHFSI_REQUIRE(A && B && X && C && evals && C != X, "bad generalized buffers");
+    cudaStream_t st = ctx->stream;
+    const size_t nn = sizeof(double2) * (size_t)n * n;
+    double2* W = (double2*)ws_get(ctx, "gen_W", nn);
+    double2* T = (double2*)ws_get(ctx, "gen_T", nn);
+    double2* Hs = (double2*)ws_get(ctx, "gen_H", nn);
+    if (any_nonfinite(ctx, (size_t)2 * n * n, B))
+      throw ChfsiError{CHFSI_ENAN, "NaN/Inf in B"};
+    // B = R^H R, W = R^-1 = L^-H
+    CHFSI_CUDA_TRY(cudaMemcpyAsync(W, B, nn, cudaMemcpyDeviceToDevice, st));
+    const int info = cholinv_upper(ctx, n, W);
+    if (info != 0)
+      throw ChfsiError{CHFSI_EBREAKDOWN, "B is not numerically positive definite (minor " +
+                                             std::to_string(info) + ")"};
+    // H = W^H A W (= L^-1 A L^-H), Hermitianised
+    gemm_nn(ctx, n, n, n, C2(A), n, W, n, T, n);
+    gemm_cn(ctx, n, n, n, W, n, T, n, Hs, n);
+    hermitianize(st, n, Hs, n);
+    status = solve_one(ctx, Hs, n, nev, nex, C2(X), tol, evals, warm_host, stats,
+                       ctx->opts.step0);
+    // C = W Y (= L^-H Y)
+    gemm_nn(ctx, n, nev + nex, n, W, n, C2(X), n, C2(C), n);
+    CHFSI_CUDA_TRY(cudaStreamSynchronize(st));
+  });
+  if (rc != CHFSI_OK) {
+    if (stats) stats->status = rc;
+    return rc;
+  }
+  if (status == CHFSI_ENOCONV) ctx->last_error = "max_loops reached";
+  return status;
+}
+
 int chfsi_solve_sequence(chfsi_ctx* ctx, const double* const* H, int N, int n, int nev,
                          int nex, double* X, double tol, double* evals, chfsi_stats* stats) {
   if (!ctx) return CHFSI_EINVAL;

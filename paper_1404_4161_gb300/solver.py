@@ -71,6 +71,23 @@ class Chfsi:
         self._check(rc, allow)
         return ev, st.as_dict(), rc
 
+    def solve_generalized(self, Ac, Bc, nev, nex, Xc, tol, warm=None, allow=(L.ENOCONV,)):
+        """A c = lam B c: Ac, Bc colmajor (n, n); Xc colmajor starting block of
+        the standard form, overwritten with its Ritz vectors.  Returns
+        (evals, C colmajor (k, n), stats, rc)."""
+        n = Ac.shape[0]
+        k = nev + nex
+        ev = torch.empty(k, dtype=torch.float64, device=Ac.device)
+        Cc = torch.empty_like(Xc)
+        st = Stats()
+        w = (C.c_double * 2)(*warm) if warm is not None else None
+        rc = self.lib.chfsi_solve_generalized(self.ctx, _ptr(Ac), _ptr(Bc), n, nev, nex, _ptr(Xc),
+                                              _ptr(Cc), tol, _ptr(ev),
+                                              C.cast(w, C.c_void_p) if w is not None else None,
+                                              C.byref(st))
+        self._check(rc, allow)
+        return ev, Cc, st.as_dict(), rc
+
     def solve_sequence(self, Hcs, nev, nex, Xc, tol, allow=(L.ENOCONV,)):
         N = len(Hcs)
         n = Hcs[0].shape[0]
