@@ -139,8 +139,9 @@ typedef struct chfsi_stats {
   double k_tc_ms;           /* tcgen05 filter-step kernel                */
   double k_tc_flops;        /* its useful complex flops, 8 n^2 k_active  */
   long long k_tc_launches;
-  double k_solver_ms;       /* cuSOLVER calls: the FP32 start of the      */
-                            /* reduced eigensolve on dense quotients      */
+  double k_solver_ms;       /* FP32 start of the reduced eigensolve on    */
+                            /* dense quotients (tridiagonal reduction and */
+                            /* the tridiagonal eigenpairs)                */
   long long k_solver_calls;
   int loops_mlp;            /* loops whose degrees came from the MLP     */
   int mlp_fallback;         /* 1 if the MLP stalled and the analytic rule */

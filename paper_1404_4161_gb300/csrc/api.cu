@@ -149,36 +149,6 @@ void filter_f64(chfsi_ctx* ctx, const double2* H, int n, int k, const double2* Y
   filter_f64_recurrence(ctx->stream, H, n, k, Y0, deg, lam1, c, e, Yout, F);
 }
 
-// ------------------------------------------------- cuSOLVER helpers ----
-int* dev_info(chfsi_ctx* ctx) { return (int*)ws_get(ctx, "solver_info", sizeof(int) * 4); }
-
-int read_info(chfsi_ctx* ctx) {
-  int* h = (int*)pinned_get(ctx, 64);
-  CHFSI_CUDA_TRY(cudaMemcpyAsync(h, dev_info(ctx), sizeof(int), cudaMemcpyDeviceToHost,
-                                 ctx->stream));
-  CHFSI_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
-  return *h;
-}
-
-
-// Hermitian eigensolve of G (k x k, lower part read): eigenvectors overwrite G.
-void heevd(chfsi_ctx* ctx, int k, double2* G, double* w) {
-  int lwork = 0;
-  CHFSI_SOLVER_TRY(cusolverDnZheevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR,
-                                               CUBLAS_FILL_MODE_LOWER, k, (cuDoubleComplex*)G,
-                                               k, w, &lwork));
-  void* work = ws_get(ctx, "heevd_work", sizeof(cuDoubleComplex) * (size_t)std::max(lwork, 1));
-  const int slot = kt_begin(ctx->stream);
-  CHFSI_SOLVER_TRY(cusolverDnZheevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR,
-                                    CUBLAS_FILL_MODE_LOWER, k, (cuDoubleComplex*)G, k, w,
-                                    (cuDoubleComplex*)work, lwork, dev_info(ctx)));
-  kt_end(ctx->stream, slot, KT_SOLVER, 0.0);
-  const int info = read_info(ctx);
-  if (info != 0)
-    throw ChfsiError{CHFSI_ECUDA, "reduced eigensolve failed (info " + std::to_string(info) +
-                                      ")"};
-}
-
 // ------------------------------------------------ FP64 product engines ----
 bool use_oz(chfsi_ctx* ctx) { return ctx->opts.f64_gemm == CHFSI_GEMM_OZAKI; }
 
@@ -356,10 +326,7 @@ void rayleigh_ritz_dev(chfsi_ctx* ctx, const double2* H, int n, int k, const dou
   // The reduced eigensolver is iterative: never hand it NaN or Inf.
   if (any_nonfinite(ctx, (size_t)2 * k * k, (const double*)G))
     throw ChfsiError{CHFSI_ENAN, "NaN/Inf in the Rayleigh quotient"};
-  if (use_oz(ctx))
-    reduced_eigh_mixed(ctx, k, G, evals);
-  else
-    heevd(ctx, k, G, evals);
+  reduced_eigh_mixed(ctx, k, G, evals, !use_oz(ctx));
   gemm_nn(ctx, n, k, k, Q, n, G, k, Y, n);
   gemm_nn(ctx, n, k, k, Z, n, G, k, HY, n);
 }
@@ -963,8 +930,6 @@ int chfsi_init(chfsi_ctx** out, const chfsi_opts* opts, void* stream) {
     ctx->sm_count = p.multiProcessorCount;
     ctx->cc_major = p.major;
     ctx->cc_minor = p.minor;
-    CHFSI_SOLVER_TRY(cusolverDnCreate(&ctx->solver));
-    CHFSI_SOLVER_TRY(cusolverDnSetStream(ctx->solver, ctx->stream));
     for (auto& e : ctx->ev) CHFSI_CUDA_TRY(cudaEventCreate(&e));
     if (ctx->opts.precision != CHFSI_PREC_FP64 && !tc_filter_supported(ctx))
       throw ChfsiError{CHFSI_ENOTSUP, "split-precision filter needs an sm_103 device"};
@@ -997,7 +962,6 @@ void chfsi_free(chfsi_ctx* ctx) {
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   for (auto& e : ctx->ev)
     if (e) cudaEventDestroy(e);
-  if (ctx->solver) cusolverDnDestroy(ctx->solver);
   delete ctx;
 }
 

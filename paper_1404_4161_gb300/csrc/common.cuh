@@ -4,7 +4,6 @@
 #pragma once
 
 #include <cuda_runtime.h>
-#include <cusolverDn.h>
 
 #include <cstdint>
 #include <cstdio>
@@ -26,15 +25,6 @@ struct ChfsiError {
     if (e_ != cudaSuccess)                                                     \
       throw ChfsiError{CHFSI_ECUDA, std::string(#call) + ": " +                \
                                         cudaGetErrorString(e_)};               \
-  } while (0)
-
-#define CHFSI_SOLVER_TRY(call)                                                 \
-  do {                                                                         \
-    cusolverStatus_t s_ = (call);                                              \
-    if (s_ != CUSOLVER_STATUS_SUCCESS)                                         \
-      throw ChfsiError{CHFSI_ECUDA,                                            \
-                       std::string(#call) + ": cusolver status " +             \
-                           std::to_string((int)s_)};                           \
   } while (0)
 
 #define CHFSI_REQUIRE(cond, text)                                              \
@@ -103,7 +93,6 @@ struct chfsi_ctx {
   int device = 0;
   int sm_count = 0;
   int cc_major = 0, cc_minor = 0;
-  cusolverDnHandle_t solver = nullptr;
   std::string last_error;
   std::unordered_map<std::string, DevBuf> ws;
   void* pinned = nullptr;  // small page-locked control buffer
@@ -284,7 +273,13 @@ int oz_slices_for(int dim);
 int oz_check_error(chfsi_ctx* ctx);
 // Reduced Hermitian eigensolve: FP32 eigenpairs refined to FP64 accuracy
 // (eig_mixed.cu); eigenvectors overwrite G, eigenvalues ascending in w.
-void reduced_eigh_mixed(chfsi_ctx* ctx, int k, double2* G, double* w);
+// Products FP64-accurate on the tensor cores, or FP64 on the CUDA cores
+// when f64_products is set.
+void reduced_eigh_mixed(chfsi_ctx* ctx, int k, double2* G, double* w, bool f64_products);
+// FP32-accurate eigenvectors of the Hermitian G (k x k, ld k) into W (k x k,
+// ld k), columns in ascending eigenvalue order (eig_trd.cu).
+// W = Q Z runs on the engine that f64_products selects.
+void trd_eigvecs_f32(chfsi_ctx* ctx, int k, const double2* G, double2* W, bool f64_products);
 
 // Degree MLP (mlp.cu).
 void mlp_create(chfsi_ctx* ctx);

@@ -3,8 +3,9 @@
 //
 // GB300's FP64 pipe makes LAPACK-style k x k eigensolvers slow (about
 // 14 ms at k = 320 in FP64).  Here the eigenvectors are obtained by
-// iterative refinement on the FP64-accurate tensor-core GEMM (8 slices per
-// operand, ~2^-56 of the row and column scales), after Ogita and Aishima
+// iterative refinement on FP64-accurate products -- the tensor-core GEMM
+// (8 slices per operand, ~2^-56 of the row and column scales), or FP64
+// GEMMs on the CUDA cores for the FP64 engine -- after Ogita and Aishima
 // ("Iterative refinement for symmetric eigenvalue decomposition", Japan J.
 // Indust. Appl. Math. 35, 2018; part II on clustered eigenvalues, 36, 2019),
 // written here for complex Hermitian matrices.  One iteration, for the
@@ -30,10 +31,8 @@
 // Start: W = I when G itself has no hard pair more than 16 positions apart
 // (the warm Rayleigh quotients of a sequence are nearly diagonal: only
 // near-degenerate pairs need the cluster step); otherwise the FP32
-// eigenvectors of G (cuSOLVER cheevd).  The eigenvalues returned are the
-// Rayleigh quotients lam_i of the final W.
-#include <cuComplex.h>
-
+// eigenvectors of G from a Householder tridiagonal reduction (eig_trd.cu).
+// The eigenvalues returned are the Rayleigh quotients lam_i of the final W.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -78,18 +77,6 @@ __device__ __forceinline__ int warp_sum(int v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
-}
-
-__global__ void to_c64_kernel(size_t n, const double2* __restrict__ a, cuComplex* __restrict__ b) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x)
-    b[i] = make_cuComplex((float)a[i].x, (float)a[i].y);
-}
-
-__global__ void to_c128_kernel(size_t n, const cuComplex* __restrict__ a, double2* __restrict__ b) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x)
-    b[i] = make_double2((double)a[i].x, (double)a[i].y);
 }
 
 // lam_i = Re s_ii / Re m_ii; max |lam| and the diagonal part of max |M - I|.
@@ -467,7 +454,7 @@ struct EvHost {
 }  // namespace
 
 // Eigenvalues (ascending) into w, eigenvectors into G (k x k, ld k).
-void reduced_eigh_mixed(chfsi_ctx* ctx, int k, double2* G, double* w) {
+void reduced_eigh_mixed(chfsi_ctx* ctx, int k, double2* G, double* w, bool f64_products) {
   cudaStream_t st = ctx->stream;
   const size_t kk = (size_t)k * k;
   double2* W = (double2*)ws_get(ctx, "eig_W", sizeof(double2) * kk);
@@ -513,36 +500,35 @@ void reduced_eigh_mixed(chfsi_ctx* ctx, int k, double2* G, double* w) {
     h.max_cluster = ctl_h->max_cluster;
     return h;
   };
+  // k x k products: FP64-accurate on the tensor cores (8 slices) or FP64
+  // on the CUDA cores.  C = A B + beta C, and C = A^H B.
+  auto gnn = [&](const double2* A, const double2* B, double2* C, double beta) {
+    if (!f64_products) {
+      oz_gemm_nn(ctx, k, k, k, A, k, B, k, C, k, 1.0, beta, 8);
+      return;
+    }
+    EpiNN ep;
+    ep.beta = beta;
+    ep.P = beta != 0.0 ? C : nullptr;
+    ep.ldp = k;
+    ep.D = C;
+    ep.ldd = k;
+    zgemm_nn(st, k, k, k, A, k, B, k, ep);
+  };
+  auto gcn = [&](const double2* A, const double2* B, double2* C) {
+    if (f64_products)
+      zgemm_cn(ctx, k, k, k, A, k, B, k, C, k, 1.0, 0.0);
+    else
+      oz_gemm_cn(ctx, k, k, k, A, k, B, k, C, k, 1.0, 0.0, 8);
+  };
   auto products = [&]() {
-    oz_gemm_nn(ctx, k, k, k, G, k, W, k, GW, k, 1.0, 0.0, 8);  // G W
-    oz_gemm_cn(ctx, k, k, k, W, k, GW, k, S, k, 1.0, 0.0, 8);  // S = W^H G W
-    oz_gemm_cn(ctx, k, k, k, W, k, W, k, M, k, 1.0, 0.0, 8);   // M = W^H W
+    gnn(G, W, GW, 0.0);  // G W
+    gcn(W, GW, S);       // S = W^H G W
+    gcn(W, W, M);        // M = W^H W
   };
-  // FP32 eigenvectors of G as the starting W (cuSOLVER cheevd).
-  auto fp32_start = [&]() {
-    cuComplex* G32 = (cuComplex*)ws_get(ctx, "eig_g32", sizeof(cuComplex) * kk);
-    float* w32 = (float*)ws_get(ctx, "eig_w32", sizeof(float) * k);
-    to_c64_kernel<<<grid_k2(k), 256, 0, st>>>(kk, G, G32);
-    chfsi_check_launch("to_c64");
-    int lwork = 0;
-    CHFSI_SOLVER_TRY(cusolverDnCheevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR,
-                                                 CUBLAS_FILL_MODE_LOWER, k, G32, k, w32, &lwork));
-    cuComplex* work =
-        (cuComplex*)ws_get(ctx, "eig_work32", sizeof(cuComplex) * (size_t)std::max(lwork, 1));
-    int* info = (int*)ws_get(ctx, "eig_info", sizeof(int));
-    const int slot = kt_begin(st);
-    CHFSI_SOLVER_TRY(cusolverDnCheevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR,
-                                      CUBLAS_FILL_MODE_LOWER, k, G32, k, w32, work, lwork, info));
-    kt_end(st, slot, KT_SOLVER, 0.0);
-    to_c128_kernel<<<grid_k2(k), 256, 0, st>>>(kk, G32, W);
-    chfsi_check_launch("to_c128");
-    int* hinfo = (int*)pinned_get(ctx, 64) + 32;
-    CHFSI_CUDA_TRY(cudaMemcpyAsync(hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CHFSI_CUDA_TRY(cudaStreamSynchronize(st));
-    if (*hinfo != 0)
-      throw ChfsiError{CHFSI_ECUDA,
-                       "FP32 reduced eigensolve failed (info " + std::to_string(*hinfo) + ")"};
-  };
+  // FP32 eigenvectors of G as the starting W (Householder tridiagonal
+  // reduction, tridiagonal eigenpairs, back transformation: eig_trd.cu).
+  auto fp32_start = [&]() { trd_eigvecs_f32(ctx, k, G, W, f64_products); };
 
   bool identity = true;   // W = I (not materialised: S = G, M = I)
   bool tried_fp32 = false;
@@ -611,8 +597,8 @@ void reduced_eigh_mixed(chfsi_ctx* ctx, int k, double2* G, double* w) {
       oa_e_kernel<<<grid_k2(k), 256, 0, st>>>(k, S, M, lam, E);
       chfsi_check_launch("oa_e");
       CHFSI_CUDA_TRY(cudaMemcpyAsync(W2, W, sizeof(double2) * kk, cudaMemcpyDeviceToDevice, st));
-      oz_gemm_nn(ctx, k, k, k, W, k, E, k, W2, k, 1.0, 1.0, 8);  // W + W E
-      oz_gemm_cn(ctx, k, k, k, W2, k, W2, k, M, k, 1.0, 0.0, 8);
+      gnn(W, E, W2, 1.0);  // W + W E
+      gcn(W2, W2, M);
     } else {
       // only orthonormality is left
       CHFSI_CUDA_TRY(cudaMemcpyAsync(W2, W, sizeof(double2) * kk, cudaMemcpyDeviceToDevice, st));
@@ -620,7 +606,7 @@ void reduced_eigh_mixed(chfsi_ctx* ctx, int k, double2* G, double* w) {
     // Newton-Schulz: W <- W2 (3I - W2^H W2) / 2
     ns_kernel<<<grid_k2(k), 256, 0, st>>>(k, M, E);
     chfsi_check_launch("ns");
-    oz_gemm_nn(ctx, k, k, k, W2, k, E, k, W, k, 1.0, 0.0, 8);
+    gnn(W2, E, W, 0.0);
   }
   if (identity) shift_identity(st, k, nullptr, 1.0, W);
   if (!fresh) {  // the iteration limit was hit after an update: final quotients
@@ -630,6 +616,11 @@ void reduced_eigh_mixed(chfsi_ctx* ctx, int k, double2* G, double* w) {
   // ascending order
   gather_values(st, k, lam, perm, w);
   gather_columns(st, k, k, W, k, perm, G, k);
+  if (f64_products) {
+    CHFSI_CUDA_TRY(cudaStreamSynchronize(st));
+    return;
+  }
+  // the error word of the tensor-core GEMM is only written by its launches
   const int e = oz_check_error(ctx);  // also synchronises
   if (e)
     throw ChfsiError{CHFSI_ETIMEOUT, "tensor-core GEMM: a bounded wait gave up (code " +
