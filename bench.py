@@ -79,6 +79,14 @@ def parse():
     ap.add_argument("--train-length", type=int, default=None,
                     help="problems in the (separate) training sequence of the degree MLP "
                          "(default: the sequence length, so training covers every step index)")
+    ap.add_argument("--filter-probe", action="store_true",
+                    help="time the tensor-core filter alone on one fixed shape (uniform "
+                         "degree, so the work per launch is exact) and print its own JSON "
+                         "line; the sequence benchmark is not run")
+    ap.add_argument("--probe-k", type=int, default=320)
+    ap.add_argument("--probe-deg", type=int, default=8)
+    ap.add_argument("--probe-split", choices=["x3", "x6"], default="x3")
+    ap.add_argument("--probe-reps", type=int, default=5)
     return ap.parse_args()
 
 
@@ -442,10 +450,74 @@ def measure_batched_full(dev, stream, problems=64, steps=10, window=2, oracle_sa
     return out
 
 
+def filter_probe(args):
+    """One filter shape, chfsi_filter with the tensor-core split product: a
+    random Hermitian H (n x n), a random block Y0 (n x k), every column of
+    degree m.  Per launch the method's complex work is 8 n^2 k m flops (m
+    products H Y of k columns); the tensor cores execute 3x (BF16x3) or 6x
+    (BF16x6) that in BF16 products.  The timed call also repacks H into its
+    bf16 pieces and splits Y0; the kernel's own share comes from the
+    library's kernel timer (filter launches only)."""
+    import torch
+    from paper_1404_4161_gb300.build import build
+    build()
+    from paper_1404_4161_gb300 import _lib as L
+    from paper_1404_4161_gb300.solver import Chfsi, colmajor
+    from workloads.synthetic import random_block
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n, k, m = args.n or 4096, args.probe_k, args.probe_deg
+    g = torch.Generator(device=dev).manual_seed(14044161 + 77)
+    A = torch.randn(n, n, dtype=torch.complex128, device=dev, generator=g)
+    H = (A + A.conj().t()) / (2.0 * n ** 0.5)  # spectrum within about [-2, 2]
+    del A
+    Hc = colmajor(H)
+    del H
+    Y0c = colmajor(torch.from_numpy(random_block(n, k, 14044161 + 78)).to(dev))
+    split = L.SPLIT_BF16X3 if args.probe_split == "x3" else L.SPLIT_BF16X6
+    s = Chfsi(precision=L.PREC_MIXED, split=split, profile=1)
+    lz = s.lanczos(Hc, 20, 14044161 + 79)
+    lo, hi = lz["theta_min"], lz["beta"]
+    cut = lo + 0.1 * (hi - lo)  # filter interval [cut, hi], lam1 = lo
+    c, e = 0.5 * (cut + hi), 0.5 * (hi - cut)
+    deg = [m] * k
+    stream = torch.cuda.current_stream()
+    for _ in range(3):  # the first call also tunes the tiling of this shape
+        out = s.filter(Hc, Y0c, deg, lo, c, e, precision=L.PREC_MIXED)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.probe_reps):
+        out = s.filter(Hc, Y0c, deg, lo, c, e, precision=L.PREC_MIXED)
+    b.record(stream)
+    torch.cuda.synchronize()
+    call_ms = a.elapsed_time(b) / args.probe_reps
+    if not bool(torch.isfinite(torch.view_as_real(out)).all()):
+        raise RuntimeError("filter probe: non-finite output")
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    pk = peaks.get("bf16_tflops", 1900.0)
+    useful = 8.0 * n * n * k * m
+    mult = 3.0 if split == L.SPLIT_BF16X3 else 6.0
+    ex = useful * mult / (call_ms / 1e3) / 1e12
+    print(json.dumps({"probe": "tc_filter_kernel via chfsi_filter", "n": n, "k": k, "degree": m,
+                      "split": args.probe_split, "reps": args.probe_reps,
+                      "ms_per_call": call_ms, "useful_tflops": useful / (call_ms / 1e3) / 1e12,
+                      "executed_tflops": ex, "peak_bf16_burst": pk, "frac_of_burst": ex / pk,
+                      "note": "call time includes the repack of H and the split of Y0",
+                      "tiling": s.autotune_table()}))
+    s.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.filter_probe:
+        return filter_probe(args)
     import torch
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -638,7 +710,7 @@ def main():
     # every timed kernel family, library or not; the roofline object is the
     # family with the most device time among those with a roofline
     kernel_ms = {"ozaki_gemm" if f64g == L.GEMM_OZAKI else "fp64_gemm": k64_ms,
-                 "tc_filter": ktc_ms, "cusolver_fp32_eig_start": tot("k_solver_ms"),
+                 "tc_filter": ktc_ms, "fp32_eig_start": tot("k_solver_ms"),
                  "cholinv": tot("k_cholinv_ms"), "lanczos": lz_ms,
                  "ozaki_slicers": tot("k_slice_ms"), "eig_control": tot("k_eigctl_ms")}
     kernel_ms["other (phases minus the above)"] = max(0.0, sum(

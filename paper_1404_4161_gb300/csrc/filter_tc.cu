@@ -197,6 +197,11 @@ __device__ __forceinline__ void split_pieces(float x, __nv_bfloat16 (&q)[MAX_PIE
 // bias is relative to their own, 2^-8 smaller, sum).
 constexpr int SLOT = 128;
 constexpr int RING = 2;
+// complex columns per batch of the epilogue's loads (register budget)
+template <int NS>
+struct EpGrp {
+  static constexpr int value = NS == 2 ? 8 : 4;
+};
 
 template <int NS>
 struct ChunkCfg {
@@ -209,6 +214,7 @@ tc_filter_kernel(const FProb* __restrict__ probs, const FSeg* __restrict__ segs,
                  int total_tiles, const CUtensorMap* __restrict__ maps, int nmax, int stages,
                  int* done, int* abort_g_ptr, int* err) {
   constexpr int CKB = ChunkCfg<NS>::KB;
+  constexpr int EP_GRP = EpGrp<NS>::value;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t a_bytes = BM * BK * 2;
@@ -398,41 +404,64 @@ tc_filter_kernel(const FProb* __restrict__ probs, const FSeg* __restrict__ segs,
         float2* next = pr.M + (size_t)sg.next * nk;
         const float2* Rf = sg.fR ? pr.Rf : nullptr;
         __nv_bfloat16* bo = pr.B + (size_t)(3 * sg.bout) * pr.b_elems;
+        // columns in batches of EP_GRP: the batch's loads are issued
+        // together (L2, coherent with the other SMs' stores), then the
+        // recurrence and the stores, so a tile pays a few L2 latencies
+        // instead of one per column
 #pragma unroll
-        for (int c2 = 0; c2 < SLOT; c2 += 2) {
-          const int rc = g.cs + c2;  // real column (even)
-          if (rc < g.ce) {
-            const int j = rc >> 1;  // complex column
-            const size_t e = (size_t)row + (size_t)j * n;
-            const float2 cu = cur[e];
-            float re = sg.a * (acc[c2] - sg.c * cu.x);
-            float im = sg.a * (acc[c2 + 1] - sg.c * cu.y);
-            if (prev) {
-              const float2 pv = prev[e];
-              re = fmaf(sg.b, pv.x, re);
-              im = fmaf(sg.b, pv.y, im);
-            }
-            if (Rf) {
-              const float f = (float)sg.fR[j];
-              const float2 rr = Rf[e];
-              re = fmaf(f, rr.x, re);
-              im = fmaf(f, rr.y, im);
-            }
-            next[e] = make_float2(re, im);
-            __nv_bfloat16 pre[MAX_PIECES], pim[MAX_PIECES], pnim[MAX_PIECES];
-            split_pieces(re, pre);
-            split_pieces(im, pim);
-            split_pieces(-im, pnim);
-            const size_t r0 = (size_t)(2 * j) * pr.P, r1 = r0 + pr.P;
+        for (int cb = 0; cb < SLOT; cb += 2 * EP_GRP) {
+          if (g.cs + cb >= g.ce) continue;  // uniform across the CTA
+          float2 cu[EP_GRP], pv[EP_GRP], rr[EP_GRP];
+          float fr[EP_GRP];
 #pragma unroll
-            for (int pc = 0; pc < NS; ++pc) {
-              __nv_bfloat16* bq = bo + (size_t)pc * pr.b_elems;
-              bq[r0 + row] = pre[pc];       // column 2j, top:      Yr
-              bq[r1 + n + row] = pre[pc];   // column 2j+1, bottom: Yr
-              bq[r1 + row] = pim[pc];       // column 2j+1, top:    Yi
-              bq[r0 + n + row] = pnim[pc];  // column 2j, bottom:   -Yi
+          for (int u = 0; u < EP_GRP; ++u) {
+            const int rc = g.cs + cb + 2 * u;
+            cu[u] = pv[u] = rr[u] = make_float2(0.f, 0.f);
+            fr[u] = 0.f;
+            if (rc < g.ce) {
+              const int j = rc >> 1;
+              const size_t e = (size_t)row + (size_t)j * n;
+              cu[u] = __ldcg(cur + e);
+              if (prev) pv[u] = __ldcg(prev + e);
+              if (Rf) {
+                rr[u] = __ldcg(Rf + e);
+                fr[u] = (float)__ldg(sg.fR + j);
+              }
             }
-            if (j < sg.s_new) pr.out[e] = make_double2((double)re, (double)im);
+          }
+#pragma unroll
+          for (int u = 0; u < EP_GRP; ++u) {
+            const int c2 = cb + 2 * u;
+            const int rc = g.cs + c2;  // real column (even)
+            if (rc < g.ce) {
+              const int j = rc >> 1;  // complex column
+              const size_t e = (size_t)row + (size_t)j * n;
+              float re = sg.a * (acc[c2] - sg.c * cu[u].x);
+              float im = sg.a * (acc[c2 + 1] - sg.c * cu[u].y);
+              if (prev) {
+                re = fmaf(sg.b, pv[u].x, re);
+                im = fmaf(sg.b, pv[u].y, im);
+              }
+              if (Rf) {
+                re = fmaf(fr[u], rr[u].x, re);
+                im = fmaf(fr[u], rr[u].y, im);
+              }
+              next[e] = make_float2(re, im);
+              __nv_bfloat16 pre[MAX_PIECES], pim[MAX_PIECES], pnim[MAX_PIECES];
+              split_pieces(re, pre);
+              split_pieces(im, pim);
+              split_pieces(-im, pnim);
+              const size_t r0 = (size_t)(2 * j) * pr.P, r1 = r0 + pr.P;
+#pragma unroll
+              for (int pc = 0; pc < NS; ++pc) {
+                __nv_bfloat16* bq = bo + (size_t)pc * pr.b_elems;
+                bq[r0 + row] = pre[pc];       // column 2j, top:      Yr
+                bq[r1 + n + row] = pre[pc];   // column 2j+1, bottom: Yr
+                bq[r1 + row] = pim[pc];       // column 2j+1, top:    Yi
+                bq[r0 + n + row] = pnim[pc];  // column 2j, bottom:   -Yi
+              }
+              if (j < sg.s_new) pr.out[e] = make_double2((double)re, (double)im);
+            }
           }
         }
       }
