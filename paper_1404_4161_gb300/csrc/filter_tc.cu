@@ -184,37 +184,57 @@ __device__ __forceinline__ void split_pieces(float x, __nv_bfloat16 (&q)[MAX_PIE
   q[2] = __float2bfloat16_rn(r1 - __bfloat162float(q[1]));
 }
 
-// Accumulator slots: TMEM holds RING slots of 2 x SLOT columns (2 x 256 =
-// 512).  A tile's K range is cut into chunks of ChunkCfg::KB K blocks; chunk g
-// (counted over all tiles of the CTA) accumulates into slot g % RING -- the
-// leading product x0 y0 into its first SLOT columns, the smaller products
-// into the second -- and is drained by the epilogue warps into FP32
-// registers (round-to-nearest adds).  The tensor cores' FP32 accumulation
-// rounds toward zero (a bias of about 0.3 ulp of the running sum per
-// accumulate); draining every chunk bounds that bias by the chunk's
-// accumulates instead of the whole K range, and keeping the leading product
-// apart leaves its sum one accumulate per 16 of K (the smaller products'
-// bias is relative to their own, 2^-8 smaller, sum).
-constexpr int SLOT = 128;
+// Accumulator slots: TMEM (512 columns) holds RING = 2 slots.  A tile's K
+// range is cut into chunks of KCfg::KB K blocks; chunk g (counted over all
+// tiles of the CTA) accumulates into slot g % RING and is drained by the
+// epilogue warps into FP32 registers (round-to-nearest adds).  The tensor
+// cores' FP32 accumulation rounds toward zero (a bias of about 0.3 ulp of
+// the running sum per accumulate); draining every chunk bounds that bias by
+// the chunk's accumulates instead of the whole K range.
+//   * Three products (NS = 2): one accumulator of up to 256 columns per slot
+//     (a 128 x 256 output tile); the chunk's 96 accumulates leave a bias
+//     of about 2e-6 of the chunk sum, within the format's 2^-16.  Sixteen
+//     epilogue warps, four per TMEM lane quarter, 64 columns each.
+//   * Six products (NS = 3): two accumulators of 128 columns per slot, the
+//     leading product x0 y0 in the first (its sum sees one accumulate per 16
+//     of K) and the smaller products in the second (their bias is relative
+//     to their own, 2^-8 smaller, sum).  Four epilogue warps, 128 columns
+//     each.
 constexpr int RING = 2;
-// complex columns per batch of the epilogue's loads (register budget)
 template <int NS>
-struct EpGrp {
-  static constexpr int value = NS == 2 ? 8 : 4;
+struct KCfg;
+template <>
+struct KCfg<2> {
+  static constexpr int SLOT = 256;  // accumulator columns
+  static constexpr int NACC = 1;    // accumulators per slot
+  static constexpr int EPW = 16;    // epilogue warps
+  static constexpr int KB = 8;      // K blocks (64 wide) per chunk
+  static constexpr int EP_GRP = 1;  // complex columns per batch of the epilogue's loads
 };
+template <>
+struct KCfg<3> {
+  static constexpr int SLOT = 128;
+  static constexpr int NACC = 2;
+  static constexpr int EPW = 4;
+  static constexpr int KB = 4;
+  static constexpr int EP_GRP = 4;
+};
+template <int NS>
+constexpr int kthreads() {
+  return 128 + 32 * KCfg<NS>::EPW;
+}
 
 template <int NS>
-struct ChunkCfg {
-  static constexpr int KB = NS == 2 ? 8 : 4;  // K blocks (64 wide) per chunk
-};
-
-template <int NS>
-__global__ void __launch_bounds__(NTHREADS, 1)
+__global__ void __launch_bounds__(kthreads<NS>(), 1)
 tc_filter_kernel(const FProb* __restrict__ probs, const FSeg* __restrict__ segs, int nsegs,
                  int total_tiles, const CUtensorMap* __restrict__ maps, int nmax, int stages,
                  int* done, int* abort_g_ptr, int* err) {
-  constexpr int CKB = ChunkCfg<NS>::KB;
-  constexpr int EP_GRP = EpGrp<NS>::value;
+  constexpr int CKB = KCfg<NS>::KB;
+  constexpr int EP_GRP = KCfg<NS>::EP_GRP;
+  constexpr int SLOT = KCfg<NS>::SLOT;
+  constexpr int NACC = KCfg<NS>::NACC;
+  constexpr int EPW = KCfg<NS>::EPW;
+  constexpr int CW = SLOT * 4 / EPW;  // accumulator columns per epilogue thread
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t a_bytes = BM * BK * 2;
@@ -224,7 +244,7 @@ tc_filter_kernel(const FProb* __restrict__ probs, const FSeg* __restrict__ segs,
   uint64_t* full = bars;
   uint64_t* empty = bars + stages;
   uint64_t* sfull = bars + 2 * stages;  // [RING]
-  uint64_t* sempty = sfull + RING;      // [RING], 4 arrivals (epilogue warps)
+  uint64_t* sempty = sfull + RING;      // [RING], EPW arrivals (epilogue warps)
   uint64_t* fin = sempty + RING;        // MMA completion before TMEM release
   uint32_t* tmem_slot = (uint32_t*)(fin + 1);
   volatile int* abort_sh = (volatile int*)(tmem_slot + 1);
@@ -239,14 +259,14 @@ tc_filter_kernel(const FProb* __restrict__ probs, const FSeg* __restrict__ segs,
     }
     for (int r = 0; r < RING; ++r) {
       mbar_init(&sfull[r], 1);
-      mbar_init(&sempty[r], 4);
+      mbar_init(&sempty[r], EPW);
     }
     mbar_init(fin, 1);
     for (int i = 0; i < 8; ++i) ep_count[i] = 0;
     *abort_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 2) tmem_alloc(tmem_slot, RING * 2 * SLOT);
+  if (warp == 2) tmem_alloc(tmem_slot, RING * NACC * SLOT);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -314,8 +334,8 @@ tc_filter_kernel(const FProb* __restrict__ probs, const FSeg* __restrict__ segs,
           break;
         }
         tc_fence_after();
-        const uint32_t d_lead = tmem + (uint32_t)(slot * 2 * SLOT);
-        const uint32_t d_tail = d_lead + SLOT;
+        const uint32_t d_lead = tmem + (uint32_t)(slot * NACC * SLOT);
+        const uint32_t d_tail = NACC == 2 ? d_lead + SLOT : d_lead;
         const int kend = min(pr.kblocks, kc + CKB);
         for (int kb = kc; kb < kend; ++kb, ++kbg) {
           const int s = (int)(kbg % (uint32_t)stages);
@@ -339,9 +359,10 @@ tc_filter_kernel(const FProb* __restrict__ probs, const FSeg* __restrict__ segs,
 #pragma unroll
               for (int qa = 0; qa <= ssum; ++qa) {
                 const int qb = ssum - qa;
+                // one shared accumulator: only the leading product starts it
                 umma_bf16(d_tail, desc_sw128(sa + qa * a_bytes) + adv,
                           desc_sw128(sb + qb * bmax_bytes) + adv, idesc,
-                          (ssum == 1 && qa == 0) ? acc0 : 1u);
+                          (NACC == 2 && ssum == 1 && qa == 0) ? acc0 : 1u);
               }
             }
           }
@@ -358,16 +379,17 @@ tc_filter_kernel(const FProb* __restrict__ probs, const FSeg* __restrict__ segs,
   } else if (warp >= 4) {
     // ---------------- epilogue ----------------
     const int q = warp & 3;
+    const int col0 = ((warp - 4) >> 2) * CW;  // this warp's columns [col0, col0 + CW)
     uint32_t tc = 0, gch = 0;
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++tc) {
       const int si = find_seg(segs, nsegs, t);
       const FSeg& sg = segs[si];
       const FProb& pr = probs[sg.p];
       const TileGeo g = tile_geo(sg, pr, t);
-      const int width = g.ce - g.cs;
-      float acc[SLOT];
+      const int width = g.ce - g.cs - col0;
+      float acc[CW];
 #pragma unroll
-      for (int c = 0; c < SLOT; ++c) acc[c] = 0.f;
+      for (int c = 0; c < CW; ++c) acc[c] = 0.f;
       bool ok = true;
       for (int kc = 0; kc < pr.kblocks; kc += CKB, ++gch) {
         const int slot = (int)(gch % RING);
@@ -376,16 +398,23 @@ tc_filter_kernel(const FProb* __restrict__ probs, const FSeg* __restrict__ segs,
           break;
         }
         tc_fence_after();
-        const uint32_t tq = tmem + (uint32_t)(slot * 2 * SLOT) + ((uint32_t)(q * 32) << 16);
+        const uint32_t tq =
+            tmem + (uint32_t)(slot * NACC * SLOT + col0) + ((uint32_t)(q * 32) << 16);
 #pragma unroll
-        for (int c0 = 0; c0 < SLOT; c0 += 16) {
+        for (int c0 = 0; c0 < CW; c0 += 16) {
           if (c0 < width) {  // uniform across the warp
-            float v[16], w[16];
+            float v[16];
             __syncwarp();
             tmem_ld16(tq + (uint32_t)c0, v);  // warp-collective
-            tmem_ld16(tq + (uint32_t)(SLOT + c0), w);
+            if (NACC == 2) {
+              float w[16];
+              tmem_ld16(tq + (uint32_t)(SLOT + c0), w);
 #pragma unroll
-            for (int c = 0; c < 16; ++c) acc[c0 + c] += v[c] + w[c];
+              for (int c = 0; c < 16; ++c) acc[c0 + c] += v[c] + w[c];
+            } else {
+#pragma unroll
+              for (int c = 0; c < 16; ++c) acc[c0 + c] += v[c];
+            }
           }
         }
         tc_fence_before();
@@ -409,13 +438,13 @@ tc_filter_kernel(const FProb* __restrict__ probs, const FSeg* __restrict__ segs,
         // recurrence and the stores, so a tile pays a few L2 latencies
         // instead of one per column
 #pragma unroll
-        for (int cb = 0; cb < SLOT; cb += 2 * EP_GRP) {
-          if (g.cs + cb >= g.ce) continue;  // uniform across the CTA
+        for (int cb = 0; cb < CW; cb += 2 * EP_GRP) {
+          if (g.cs + col0 + cb >= g.ce) continue;  // uniform across the warp
           float2 cu[EP_GRP], pv[EP_GRP], rr[EP_GRP];
           float fr[EP_GRP];
 #pragma unroll
           for (int u = 0; u < EP_GRP; ++u) {
-            const int rc = g.cs + cb + 2 * u;
+            const int rc = g.cs + col0 + cb + 2 * u;
             cu[u] = pv[u] = rr[u] = make_float2(0.f, 0.f);
             fr[u] = 0.f;
             if (rc < g.ce) {
@@ -431,8 +460,8 @@ tc_filter_kernel(const FProb* __restrict__ probs, const FSeg* __restrict__ segs,
           }
 #pragma unroll
           for (int u = 0; u < EP_GRP; ++u) {
-            const int c2 = cb + 2 * u;
-            const int rc = g.cs + c2;  // real column (even)
+            const int c2 = cb + 2 * u;  // index into acc
+            const int rc = g.cs + col0 + c2;  // real column (even)
             if (rc < g.ce) {
               const int j = rc >> 1;  // complex column
               const size_t e = (size_t)row + (size_t)j * n;
@@ -465,7 +494,7 @@ tc_filter_kernel(const FProb* __restrict__ probs, const FSeg* __restrict__ segs,
           }
         }
       }
-      // The last of the four epilogue warps to finish this tile publishes it
+      // The last of the epilogue warps to finish this tile publishes it
       // (no CTA barrier, so an aborting warp cannot block the others).  A
       // warp is at most RING tiles ahead of the slowest one (each tile takes
       // at least one slot), so 8 per-tile counters are never shared.
@@ -474,7 +503,7 @@ tc_filter_kernel(const FProb* __restrict__ probs, const FSeg* __restrict__ segs,
       if (lane == 0) {
         __threadfence_block();
         const int arrived = atomicAdd(&ep_count[tc & 7u], 1);
-        if (arrived == 4 * (int)(tc >> 3) + 3) {
+        if (arrived == EPW * (int)(tc >> 3) + EPW - 1) {
           __threadfence();
           red_release_add(done + sg.done_base + g.bi, 1);
         }
@@ -485,7 +514,7 @@ tc_filter_kernel(const FProb* __restrict__ probs, const FSeg* __restrict__ segs,
   __syncthreads();
   if (warp == 2) {
     tc_fence_after();
-    tmem_dealloc(tmem, RING * 2 * SLOT);
+    tmem_dealloc(tmem, RING * NACC * SLOT);
   }
 }
 
@@ -587,6 +616,8 @@ __global__ void scale_rows_kernel(int rows, int k, const double* __restrict__ ps
 // with 2k real columns: blocks of at most 128 columns, balanced.  A wider
 // block re-reads less of A per output but gives fewer, coarser dependency
 // units; 128 keeps a 320-column block in five units.
+// Column-block width of the rule: the widest balanced blocks of at most
+// 128 real columns (the autotuner may pick up to the accumulator width).
 int block_width(int k) {
   const int cols = 2 * k;
   const int nb = (cols + 127) / 128;
@@ -594,6 +625,9 @@ int block_width(int k) {
   N = (N + 15) / 16 * 16;
   return std::max(16, std::min(128, N));
 }
+
+// Widest column block the accumulator of a split format holds.
+int max_block_width(int ns) { return ns == 2 ? KCfg<2>::SLOT : KCfg<3>::SLOT; }
 
 }  // namespace
 
@@ -727,7 +761,8 @@ static void launch_with(chfsi_ctx* ctx, int P, const TcBatchItem* items, int ns,
     pr.k = k;
     pr.P = sl.P;
     pr.kblocks = (2 * n + BK - 1) / BK;
-    pr.ntile = tl.N > 0 ? std::min(tl.N, (2 * k + 15) / 16 * 16) : block_width(k);
+    pr.ntile = tl.N > 0 ? std::min(std::min(tl.N, max_block_width(ns)), (2 * k + 15) / 16 * 16)
+                        : block_width(k);
     pr.M = sl.M;
     pr.B = sl.B;
     pr.b_elems = (long long)b_el;
@@ -847,7 +882,8 @@ static void launch_with(chfsi_ctx* ctx, int P, const TcBatchItem* items, int ns,
   }
   void* kfn = ns == 2 ? (void*)tc_filter_kernel<2> : (void*)tc_filter_kernel<3>;
   int per_sm = 0;
-  CHFSI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, NTHREADS, smem));
+  const int threads = ns == 2 ? kthreads<2>() : kthreads<3>();
+  CHFSI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, threads, smem));
   if (per_sm < 1) throw ChfsiError{CHFSI_ENOTSUP, "tensor-core filter does not fit on an SM"};
   int grid = std::min(ctx->sm_count * per_sm, tiles);
   const FProb* a0 = fs->d_probs;
@@ -865,7 +901,7 @@ static void launch_with(chfsi_ctx* ctx, int P, const TcBatchItem* items, int ns,
   for (const FSeg& sg : segs)
     fl += 8.0 * (double)items[sg.p].n * items[sg.p].n * (items[sg.p].k - sg.s_col);
   const int slot = kt_begin(st);
-  CHFSI_CUDA_TRY(cudaLaunchCooperativeKernel(kfn, dim3(grid), dim3(NTHREADS), args, smem, st));
+  CHFSI_CUDA_TRY(cudaLaunchCooperativeKernel(kfn, dim3(grid), dim3(threads), args, smem, st));
   chfsi_check_launch("tc_filter");
   kt_end(st, slot, KT_TC, fl, fl * (ns == 2 ? 3.0 : 6.0));
   int* h = (int*)pinned_get(ctx, 64);
@@ -905,8 +941,9 @@ void tc_filter_launch(chfsi_ctx* ctx, int P, const TcBatchItem* items, int ns) {
       best.us = 1e30f;
       try {
         launch_with(ctx, P, items, ns, TcTiling{});  // warm-up (slot buffers, first use)
-        for (int N : {64, 96, 128})
+        for (int N : {64, 96, 128, 192, 256})
           for (int G : {1, 2, 4}) {
+            if (N > max_block_width(ns)) continue;
             if (N > (2 * items[0].k + 15) / 16 * 16 + 15) continue;
             TcTiling cand{N, G};
             CHFSI_CUDA_TRY(cudaEventRecord(e0, st));
