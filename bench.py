@@ -32,10 +32,18 @@ sys.path.insert(0, ROOT)
 METRIC = "filter TFLOP/s and s per eigenproblem at resid≤1e-10: mixed+learned vs FP64"
 UNIT = "s/eigenproblem"
 SEQ_SEED_OFFSET = 2000
-# DRAM bytes (read + write) of one tc_filter_step_kernel launch, from an ncu
-# capture of the kernel as it stands, per n (None: not captured).
-TC_FILTER_TRAFFIC: dict = {}
-TC_FILTER_TRAFFIC_NOTE = "no capture of the current filter kernel yet"
+# ncu capture of one tc_filter_kernel launch of the fixed-shape probe
+# (bench.py --filter-probe --probe-k 320 --probe-deg 8: n 4096, 8 steps on 320
+# columns, BF16x3, 128-wide column blocks), profiles/tc_filter_kernel_n4096_k320.md.
+# The bench's own filter launches mix shapes (k_act, degrees, 3 or 6 products),
+# so their per-launch traffic is not captured; this is the kernel's measured
+# traffic against its algorithmic bytes (8 n^2 + 56 n k per step).
+TC_FILTER_PROBE_TRAFFIC = {"shape": "n 4096, k 320, degree 8, BF16x3, 128-wide blocks",
+                           "dram_bytes": 2.562e9, "algorithmic_bytes": 1.661e9,
+                           "ratio": 1.54, "ncu_duration_ms": 1.038,
+                           "executed_tflops_ncu": 993.0}
+TC_FILTER_TRAFFIC_NOTE = ("per-launch traffic of the bench's mixed launches not captured; "
+                          "see probe_traffic (one captured launch of the filter probe)")
 
 
 def parse():
@@ -689,8 +697,9 @@ def main():
     if ktc_ms > 0:
         a = ktc_fx / (ktc_ms / 1e3) / 1e12  # 3 or 6 BF16 products per complex product
         tc_roof = {"bound": "tensor", "achieved": a, "peak": bf16_peak, "unit": "TFLOP/s",
-                   "frac": a / bf16_peak, "traffic": TC_FILTER_TRAFFIC.get(n),
+                   "frac": a / bf16_peak, "traffic": None,
                    "traffic_note": TC_FILTER_TRAFFIC_NOTE,
+                   "probe_traffic": TC_FILTER_PROBE_TRAFFIC,
                    "useful_tflops": ktc_fl / (ktc_ms / 1e3) / 1e12,
                    "kernel": "tc_filter_kernel (persistent, all steps of a filter call in "
                              "one launch; BF16x3 / BF16x6 tcgen05, fused recurrence)",
