@@ -941,7 +941,7 @@ void tc_filter_launch(chfsi_ctx* ctx, int P, const TcBatchItem* items, int ns) {
       best.us = 1e30f;
       try {
         launch_with(ctx, P, items, ns, TcTiling{});  // warm-up (slot buffers, first use)
-        for (int N : {64, 96, 128, 192, 256})
+        for (int N : {64, 96, 128, 160, 192, 224, 256})
           for (int G : {1, 2, 4}) {
             if (N > max_block_width(ns)) continue;
             if (N > (2 * items[0].k + 15) / 16 * 16 + 15) continue;

@@ -182,7 +182,7 @@ def test_autotuned_tiling_gives_identical_results():
             assert len(table) == 1
             t = table[0]
             assert (t["n"], t["k_bucket"], t["pieces"]) == (n, 128, 2)
-            assert t["block_width"] in (64, 96, 128) and t["group"] in (1, 2, 4)
+            assert t["block_width"] in (64, 96, 128, 160, 192, 224, 256) and t["group"] in (1, 2, 4)
         else:
             assert table == []
     assert np.array_equal(outs[0], outs[1])
