@@ -537,9 +537,10 @@ bool verbose() {
 void trd_eigvecs_f32(chfsi_ctx* ctx, int k, const double2* G, double2* W, bool f64_products) {
   cudaStream_t st = ctx->stream;
   const size_t kk = (size_t)k * k;
-  // grid: about eight rows per CTA (one per warp for the products), at most
-  // one CTA per SM; fewer CTAs make the per-step grid barrier cheaper
-  const int Gc = std::max(1, std::min(ctx->sm_count, (k + 7) / 8));
+  // grid: about four rows per CTA, at most one CTA per SM (measured at k = 320
+  // to 1000: 4 rows per CTA beat 8, whose cheaper grid barrier does not make
+  // up for the longer per-step products)
+  const int Gc = std::max(1, std::min(ctx->sm_count, (k + 3) / 4));
   const int R = (k + Gc - 1) / Gc;
   const size_t base = sizeof(float2) * 5 * (size_t)k + sizeof(double) * (2 * TRD_WARPS + 2);
   const size_t rows_bytes = sizeof(float2) * 2 * (size_t)R * k;

@@ -198,8 +198,8 @@ __device__ __forceinline__ void split_pieces(float x, __nv_bfloat16 (&q)[MAX_PIE
 //   * Six products (NS = 3): two accumulators of 128 columns per slot, the
 //     leading product x0 y0 in the first (its sum sees one accumulate per 16
 //     of K) and the smaller products in the second (their bias is relative
-//     to their own, 2^-8 smaller, sum).  Four epilogue warps, 128 columns
-//     each.
+//     to their own, 2^-8 smaller, sum).  Eight epilogue warps, two per TMEM
+//     lane quarter, 64 columns each.
 constexpr int RING = 2;
 template <int NS>
 struct KCfg;
@@ -215,9 +215,9 @@ template <>
 struct KCfg<3> {
   static constexpr int SLOT = 128;
   static constexpr int NACC = 2;
-  static constexpr int EPW = 4;
+  static constexpr int EPW = 8;
   static constexpr int KB = 4;
-  static constexpr int EP_GRP = 4;
+  static constexpr int EP_GRP = 2;
 };
 template <int NS>
 constexpr int kthreads() {
