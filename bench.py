@@ -34,14 +34,15 @@ UNIT = "s/eigenproblem"
 SEQ_SEED_OFFSET = 2000
 # ncu capture of one tc_filter_kernel launch of the fixed-shape probe
 # (bench.py --filter-probe --probe-k 320 --probe-deg 8: n 4096, 8 steps on 320
-# columns, BF16x3, 128-wide column blocks), profiles/tc_filter_kernel_n4096_k320.md.
+# columns, BF16x3, 160-wide column blocks in groups of 4),
+# profiles/tc_filter_kernel_n4096_k320.md.
 # The bench's own filter launches mix shapes (k_act, degrees, 3 or 6 products),
 # so their per-launch traffic is not captured; this is the kernel's measured
 # traffic against its algorithmic bytes (8 n^2 + 56 n k per step).
-TC_FILTER_PROBE_TRAFFIC = {"shape": "n 4096, k 320, degree 8, BF16x3, 128-wide blocks",
-                           "dram_bytes": 2.562e9, "algorithmic_bytes": 1.661e9,
-                           "ratio": 1.54, "ncu_duration_ms": 1.038,
-                           "executed_tflops_ncu": 993.0}
+TC_FILTER_PROBE_TRAFFIC = {"shape": "n 4096, k 320, degree 8, BF16x3, 160-wide blocks, group 4",
+                           "dram_bytes": 1.602e9, "algorithmic_bytes": 1.661e9,
+                           "ratio": 0.96, "ncu_duration_ms": 0.917,
+                           "executed_tflops_ncu": 1124.0}
 TC_FILTER_TRAFFIC_NOTE = ("per-launch traffic of the bench's mixed launches not captured; "
                           "see probe_traffic (one captured launch of the filter probe)")
 
@@ -291,9 +292,10 @@ def measure_learned_protocol(dev, stream, n=8192, nev=512, nex=128, length=30, t
     correlated sequence of `length` problems (circulant construction: exact
     spectrum, eigenvectors turned by ~eps per step), problems 1..train
     solved with the analytic rule while the solver records its traces, the
-    degree MLP trained on them (library kernels), then problems train+1 ..
-    length solved twice from problem train's Ritz vectors: analytic rule vs
-    learned degrees.  Loops, filter column-degrees and seconds per problem
+    degree MLP trained on them (library kernels), the learned degree's
+    margin chosen on training problems train/2+1 .. train, then problems
+    train+1 .. length solved twice from problem train's Ritz vectors:
+    analytic rule vs learned degrees.  Loops, filter column-degrees and seconds per problem
     for both; eigenvalues checked against the exact spectrum."""
     import torch
     from paper_1404_4161_gb300 import _lib as L
@@ -310,18 +312,41 @@ def measure_learned_protocol(dev, stream, n=8192, nev=512, nex=128, length=30, t
     s = Chfsi(precision=L.PREC_TC, f64_gemm=L.GEMM_OZAKI)
     s.trace_enable(1 << 21)
     X = colmajor(torch.from_numpy(random_block(n, nev + nex, BASE_SEED + 9500)).to(dev))
-    ev, sts, rc = s.solve_sequence(Hc[:train], nev, nex, X, cfg.tol)
-    if rc != L.OK:
-        raise RuntimeError(f"learned protocol: training sequence rc {rc}")
+    half = train // 2
+    ev, sts, rc = s.solve_sequence(Hc[:half], nev, nex, X, cfg.tol)
+    X_half = X.clone()  # Ritz vectors of training problem `half`
+    s.set_opts(step0=half)
+    ev, sts2, rc2 = s.solve_sequence(Hc[half:train], nev, nex, X, cfg.tol)
+    s.set_opts(step0=0)
+    if rc != L.OK or rc2 != L.OK:
+        raise RuntimeError(f"learned protocol: training sequence rc {rc}, {rc2}")
     xs, ys = learned.dataset(s)
     losses = learned.train(s, xs, ys, steps=3000, lr=2e-3)
     s.trace_enable(0)
+    # Model selection on the training problems only: the learned degree's
+    # margin (opts.mlp_extra) that solves problems half+1..train (from the
+    # Ritz vectors of problem half) fastest is kept for the evaluation.
+    sel = {}
+    for extra in (0, 1, 2):
+        s.set_opts(degree_model=L.DEG_MLP, mlp_extra=extra, step0=half)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _, stv, rcv = s.solve_sequence(Hc[half:train], nev, nex, X_half.clone(), cfg.tol)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if rcv == L.OK:
+            sel[extra] = {"s": a.elapsed_time(b) / 1e3, "loops": sum(x["loops"] for x in stv),
+                          "col_degrees": sum(x["col_degrees"] for x in stv)}
+    best_extra = min(sel, key=lambda e: sel[e]["s"]) if sel else 2
     out = {"workload": f"circulant correlated sequence, n={n}, nev={nev}, nex={nex}, "
                        f"{length} problems; trained on problems 1..{train}, evaluated on "
                        f"{train + 1}..{length}",
-           "train_rows": int(xs.shape[0]), "loss0": losses[0], "loss": losses[-1]}
+           "train_rows": int(xs.shape[0]), "loss0": losses[0], "loss": losses[-1],
+           "mlp_extra_selected_on_training": best_extra,
+           "mlp_extra_validation": {str(e): v for e, v in sel.items()}}
     for name, model in (("analytic", L.DEG_ANALYTIC), ("learned", L.DEG_MLP)):
-        s.set_opts(degree_model=model, step0=train)
+        s.set_opts(degree_model=model, step0=train, mlp_extra=best_extra)
         Xe = X.clone()
         s.solve_sequence(Hc[train:train + 1], nev, nex, Xe.clone(), cfg.tol)  # warm-up
         a = torch.cuda.Event(enable_timing=True)

@@ -41,7 +41,7 @@ extern "C" {
 #define CHFSI_EBREAKDOWN 4  /* QR breakdown: filtered block rank-deficient  */
 #define CHFSI_ENAN 5        /* NaN or Inf met in a reduction                */
 #define CHFSI_ETIMEOUT 6    /* a bounded device wait gave up                */
-#define CHFSI_ECUDA 7       /* CUDA / cuSOLVER runtime error                */
+#define CHFSI_ECUDA 7       /* CUDA runtime error                           */
 #define CHFSI_ENOTSUP 8     /* configuration not supported on this device   */
 #define CHFSI_ETOOBIG 9     /* n*k above the static scratch of               */
                             /* chfsi_filter_static (CHFSI_FILTER_STATIC_MAX_NK) */

@@ -3,11 +3,11 @@
 // Host-side orchestration of Algorithm 1 (ChFSI) of arXiv 1404.4161 over
 // device kernels: Lanczos bounds of the spectrum, the Chebyshev filter of
 // Algorithm 2, orthonormalisation against the locked block, Rayleigh-Ritz,
-// residuals, locking and degree optimisation.  Every arithmetic step runs in this library's
-// kernels; the k x k Cholesky, triangular inverse and Hermitian
-// eigensolve of the reduced problems use cuSOLVER.  The host only reads a
-// small control block per loop (converged count, interval, sorted degrees)
-// to size the next launches.
+// residuals, locking and degree optimisation.  Every arithmetic step runs in
+// this library's kernels, the k x k Cholesky inverse and the Hermitian
+// eigensolve of the reduced problems included.  The host only reads a small
+// control block per loop (converged count, interval, sorted degrees) to size
+// the next launches.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>

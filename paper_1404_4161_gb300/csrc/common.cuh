@@ -37,8 +37,9 @@ struct ChfsiError {
 // kt_begin / kt_end bracket a launch with CUDA events on its stream and
 // kt_resolve adds the elapsed times after the stream has been synchronised.
 // Categories: FP64 products (Ozaki or DFMA GEMMs), the tensor-core filter,
-// cuSOLVER calls, the inverse-Cholesky kernel, the Lanczos kernels, the
-// Ozaki operand slicers, and the control kernels of the reduced eigensolve.
+// the FP32 start of the reduced eigensolve (tridiagonal reduction and
+// eigenpairs), the inverse-Cholesky kernel, the Lanczos kernels, the Ozaki
+// operand slicers, and the control kernels of the reduced eigensolve.
 enum KtCat {
   KT_F64 = 0, KT_TC = 1, KT_SOLVER = 2, KT_CHOLINV = 3, KT_LANCZOS = 4, KT_SLICE = 5,
   KT_EIGCTL = 6, KT_NCAT = 7
