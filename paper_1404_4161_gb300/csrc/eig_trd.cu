@@ -20,10 +20,10 @@
 //     the current interval (counts of a backward stable recurrence, so the
 //     result is within a few FP32 ulps of ||T||).
 //  3. Eigenvectors of T by inverse iteration in FP64 (tridiagonal LU with
-//     partial pivoting, three solves from a pseudo-random start).  Runs of
-//     eigenvalues closer than 1e-5 ||T|| are done by one thread in order,
-//     each solve orthogonalised against the run's earlier vectors, so a run
-//     yields an orthonormal basis of its invariant subspace.
+//     partial pivoting, three solves from a pseudo-random start), all in
+//     parallel; the vectors of each run of eigenvalues closer than
+//     1e-5 ||T|| are then orthonormalised together (modified Gram-Schmidt),
+//     an orthonormal basis of the run's invariant subspace.
 //  4. W = Q Z, Z the real eigenvectors of T: on the tensor cores (the
 //     FP64-accurate complex GEMM with 6 slices) or, for the FP64 engine, as
 //     an FP64 GEMM.
@@ -365,12 +365,15 @@ __device__ __forceinline__ double start_value(int i, int j) {
   return 0.5 + (double)(z >> 11) * (1.0 / 9007199254740992.0);  // in [0.5, 1.5)
 }
 
-// Inverse iteration for the eigenvectors of T (FP64), one thread per run of
-// close eigenvalues, 32 threads per CTA (the FP64 pipe is the limit: spread
-// the threads over the SMs).  Work arrays are k x k, interleaved by slot
+// Inverse iteration for the eigenvectors of T (FP64), one thread per
+// eigenvector, 32 threads per CTA (the FP64 pipe is the limit: spread the
+// threads over the SMs).  Work arrays are k x k, interleaved by slot
 // (element i of the thread's vector at [i * k + slot]) so that a warp's
 // accesses coalesce; every recurrence carries its value in registers.
-// zt: element i of eigenvector j at zt[i * k + j].
+// zt: element i of eigenvector j at zt[i * k + j].  For a run of close
+// eigenvalues (FP32 shifts cannot tell them apart) the run's vectors come
+// from distinct pseudo-random starts, so they span the run's invariant
+// subspace; tri_runs_mgs_kernel orthonormalises them afterwards.
 __global__ void __launch_bounds__(32)
 tri_invit_kernel(int k, const double* __restrict__ d, const double* __restrict__ e,
                  const double* __restrict__ lam, const double* __restrict__ tnorm_p,
@@ -380,18 +383,12 @@ tri_invit_kernel(int k, const double* __restrict__ d, const double* __restrict__
   const int j0 = blockIdx.x * blockDim.x + threadIdx.x;
   if (j0 >= k) return;
   const double tn = fmax(*tnorm_p, DBL_MIN);
-  const double ctol = CLUSTER_REL * tn;
-  if (j0 > 0 && lam[j0] - lam[j0 - 1] < ctol) return;  // not the first of its run
-  int j1 = j0 + 1;
-  while (j1 < k && lam[j1] - lam[j1 - 1] < ctol) ++j1;
+  const int j1 = j0 + 1;
   const size_t K = (size_t)k;
   const double tiny = DBL_EPSILON * tn;
   auto rec = [&](double u) { return 1.0 / (fabs(u) < tiny ? (u < 0.0 ? -tiny : tiny) : u); };
-  double sigma_prev = -DBL_MAX;
   for (int j = j0; j < j1; ++j) {
-    double sigma = lam[j];  // distinct shifts inside a run
-    if (j > j0) sigma = fmax(sigma, sigma_prev + 10.0 * DBL_EPSILON * tn);
-    sigma_prev = sigma;
+    const double sigma = lam[j];
     // LU with partial pivoting of T - sigma I: row i of U is (1/R0, U1, U2).
     // Loops run in batches of IB rows: a batch's loads are issued together,
     // then its part of the recurrence runs on registers.
@@ -497,19 +494,43 @@ tri_invit_kernel(int k, const double* __restrict__ d, const double* __restrict__
           ss += z * z;
         }
       }
-      if (j > j0) {  // orthogonalise against the run's earlier vectors, twice
-        for (int pass = 0; pass < 2; ++pass)
-          for (int p = j0; p < j; ++p) {
-            double dot = 0.0;
-            for (int i = 0; i < k; ++i) dot += zt[(size_t)i * K + p] * ya[(size_t)i * K + j0];
-            for (int i = 0; i < k; ++i) ya[(size_t)i * K + j0] -= dot * zt[(size_t)i * K + p];
-          }
-        ss = 0.0;
-        for (int i = 0; i < k; ++i) ss += ya[(size_t)i * K + j0] * ya[(size_t)i * K + j0];
-      }
       scale = ss > 0.0 ? 1.0 / sqrt(ss) : 1.0;
     }
     for (int i = 0; i < k; ++i) zt[(size_t)i * K + j] = scale * ya[(size_t)i * K + j0];
+  }
+}
+
+// Runs of eigenvalues closer than CLUSTER_REL ||T||: modified Gram-Schmidt,
+// twice, over the run's vectors in index order (one warp per run, its lanes
+// over the rows), so the run yields an orthonormal basis of its invariant
+// subspace.
+__global__ void __launch_bounds__(256)
+tri_runs_mgs_kernel(int k, const double* __restrict__ lam, const double* __restrict__ tnorm_p,
+                    double* __restrict__ zt) {
+  const int lane = threadIdx.x & 31;
+  const int j0 = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (j0 >= k) return;  // uniform across the warp
+  const double ctol = CLUSTER_REL * fmax(*tnorm_p, DBL_MIN);
+  if (j0 > 0 && lam[j0] - lam[j0 - 1] < ctol) return;  // not the first of its run
+  int j1 = j0 + 1;
+  while (j1 < k && lam[j1] - lam[j1 - 1] < ctol) ++j1;
+  if (j1 - j0 < 2) return;
+  const size_t K = (size_t)k;
+  for (int j = j0 + 1; j < j1; ++j) {
+    for (int pass = 0; pass < 2; ++pass)
+      for (int p = j0; p < j; ++p) {
+        double dot = 0.0;
+        for (int i = lane; i < k; i += 32) dot += zt[(size_t)i * K + p] * zt[(size_t)i * K + j];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        for (int i = lane; i < k; i += 32) zt[(size_t)i * K + j] -= dot * zt[(size_t)i * K + p];
+      }
+    double ss = 0.0;
+    for (int i = lane; i < k; i += 32) ss += zt[(size_t)i * K + j] * zt[(size_t)i * K + j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    const double r = ss > 0.0 ? 1.0 / sqrt(ss) : 1.0;
+    for (int i = lane; i < k; i += 32) zt[(size_t)i * K + j] *= r;
   }
 }
 
@@ -597,6 +618,8 @@ void trd_eigvecs_f32(chfsi_ctx* ctx, int k, const double2* G, double2* W, bool f
                                                    lu + 2 * kk, lu + 3 * kk, lu + 4 * kk,
                                                    lu + 5 * kk, piv);
   chfsi_check_launch("tri_invit");
+  tri_runs_mgs_kernel<<<(unsigned)(((size_t)k * 32 + 255) / 256), 256, 0, st>>>(k, lam, tnorm, zt);
+  chfsi_check_launch("tri_runs_mgs");
   z_complex_kernel<<<(unsigned)std::min<size_t>((kk + 255) / 256, 4096), 256, 0, st>>>(k, zt, Z);
   chfsi_check_launch("z_complex");
   kt_end(st, slot, KT_SOLVER, 0.0);
