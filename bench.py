@@ -34,8 +34,7 @@ UNIT = "s/eigenproblem"
 SEQ_SEED_OFFSET = 2000
 # ncu capture of one tc_filter_kernel launch of the fixed-shape probe
 # (bench.py --filter-probe --probe-k 320 --probe-deg 8: n 4096, 8 steps on 320
-# columns, BF16x3, 160-wide column blocks in groups of 4),
-# profiles/tc_filter_kernel_n4096_k320.md.
+# columns, BF16x3, 160-wide column blocks in groups of 4).
 # The bench's own filter launches mix shapes (k_act, degrees, 3 or 6 products),
 # so their per-launch traffic is not captured; this is the kernel's measured
 # traffic against its algorithmic bytes (8 n^2 + 56 n k per step).
