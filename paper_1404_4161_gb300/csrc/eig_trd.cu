@@ -565,6 +565,8 @@ void trd_eigvecs_f32(chfsi_ctx* ctx, int k, const double2* G, double2* W, bool f
   const int R = (k + Gc - 1) / Gc;
   const size_t base = sizeof(float2) * 5 * (size_t)k + sizeof(double) * (2 * TRD_WARPS + 2);
   const size_t rows_bytes = sizeof(float2) * 2 * (size_t)R * k;
+  // the five k-vectors of a step stay in shared memory: k <= about 5600
+  CHFSI_REQUIRE(base <= 220 * 1024, "reduced eigensolve: k too large for the FP32 start");
   const bool in_smem = base + rows_bytes <= 200 * 1024;
   const size_t smem = in_smem ? base + rows_bytes : base;
   static size_t attr_smem = 0;
@@ -611,8 +613,15 @@ void trd_eigvecs_f32(chfsi_ctx* ctx, int k, const double2* G, double2* W, bool f
                                              smem, st));
   chfsi_check_launch("trd");
   if (v) CHFSI_CUDA_TRY(cudaEventRecord(t[1], st));
-  tri_bisect_kernel<<<(k + 7) / 8, 256, sizeof(float) * 2 * (size_t)k, st>>>(k, a.d, a.e, lam,
-                                                                              tnorm);
+  const size_t bis_smem = sizeof(float) * 2 * (size_t)k;  // d and e^2 of T
+  static size_t bis_attr = 0;
+  if (bis_smem > 48 * 1024 && bis_smem > bis_attr) {
+    CHFSI_CUDA_TRY(cudaFuncSetAttribute(tri_bisect_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)bis_smem));
+    bis_attr = bis_smem;
+  }
+  tri_bisect_kernel<<<(k + 7) / 8, 256, bis_smem, st>>>(k, a.d, a.e, lam, tnorm);
   chfsi_check_launch("tri_bisect");
   tri_invit_kernel<<<(k + 7) / 8, 8, 0, st>>>(k, a.d, a.e, lam, tnorm, zt, lu, lu + kk,
                                                    lu + 2 * kk, lu + 3 * kk, lu + 4 * kk,
@@ -629,7 +638,7 @@ void trd_eigvecs_f32(chfsi_ctx* ctx, int k, const double2* G, double2* W, bool f
   else
     oz_gemm_cn(ctx, k, k, k, a.Qh, k, Z, k, W, k, 1.0, 0.0, 6);
   if (v) CHFSI_CUDA_TRY(cudaEventRecord(t[3], st));
-  int* h = (int*)pinned_get(ctx, 64) + 40;
+  int* h = (int*)pinned_get(ctx, 256) + 40;
   CHFSI_CUDA_TRY(cudaMemcpyAsync(h, a.flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
   CHFSI_CUDA_TRY(cudaStreamSynchronize(st));
   if (*h)
