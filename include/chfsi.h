@@ -341,7 +341,13 @@ int chfsi_orthonormalize(chfsi_ctx* ctx, int n, int nl, const double* L, int k,
 
 /* Alg. 1: Rayleigh-Ritz on orthonormal Q (complex n x k):
  * Z = HQ, G = Q^H Z (Hermitianised), G W = W Lambda, Y = QW, HY = ZW.
- * Y and HY: complex n x k outputs; evals: k doubles, ascending. */
+ * Y and HY: complex n x k outputs; evals: k doubles, ascending.  The k x k
+ * eigensolve is this library's: FP32 eigenvectors (Householder
+ * tridiagonalisation, Sturm multisection, inverse iteration) or W = I when
+ * G is nearly diagonal, refined to FP64 accuracy (first-order updates,
+ * exact rotations on clusters of close eigenvalues, Newton-Schulz) with the
+ * products of opts.f64_gemm.  The FP32 start needs k <= about 5600
+ * (EINVAL above). */
 int chfsi_rayleigh_ritz(chfsi_ctx* ctx, const double* H, int n, int k,
                         const double* Q, double* Y, double* HY, double* evals);
 
